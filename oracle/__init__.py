@@ -1,0 +1,341 @@
+"""Oracle: plain CPU definitions of what the kNN / FoF hot path computes.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  It shares no code with
+the CUDA path (``paper_2604_05885_gb300``) and never imports it.
+
+Contents, each following the paper (jz-tree, Stuecker et al.):
+
+* Results (the method is exact, so these are the plain definitions):
+  - ``knn_brute`` / ``knn_cells``  -- k nearest neighbours, self included, ties by
+    lower index; float64 distances (Sec. III).
+  - ``fof_brute`` / ``fof_cells``  -- FoF groups at linking length b, labelled by
+    the smallest index in each group (Sec. IV, R_link and linking rule).
+* Tree (Sec. II, the plane-based hierarchy), bit-exact integer definitions:
+  - ``morton_keys``   -- 3 x 21-bit interleaved keys (Sec. II-A: integer Morton key;
+    x is the most significant coordinate, as in the z-order comparator).
+  - ``zsort``         -- stable sort by key.
+  - ``gap_levels``    -- lvl_i between sorted neighbours i-1, i (Sec. II-C, eq. lvl_i),
+    with the sentinel gaps at 0 and N.
+  - ``node_sizes``    -- n_i, the size of the smallest node holding i-1 and i
+    (Sec. II-C, l_b / r_b search).
+  - ``plane_splits``  -- spl^(p): splits with n > N_max^(p) (Sec. II-C, tree-planes,
+    N_max^(p) = N_max^(0) c^p, coarsening stops below N_target).
+  - ``plane_nodes``   -- per-node point counts and bounding boxes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "jzt_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP) into oracle/liboracle.so."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        f32p = ctypes.POINTER(ctypes.c_float)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        lib.oracle_knn_brute.argtypes = [f32p, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                         i64p, ctypes.c_int64, i32p, f64p, ctypes.c_int]
+        lib.oracle_knn_cells.argtypes = lib.oracle_knn_brute.argtypes
+        lib.oracle_fof_brute.argtypes = [f32p, ctypes.c_int64, ctypes.c_double, ctypes.c_double, i32p]
+        lib.oracle_fof_cells.argtypes = [f32p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, i32p, ctypes.c_int]
+        lib.oracle_num_threads.argtypes = [ctypes.c_int]
+        for f in (lib.oracle_knn_brute, lib.oracle_knn_cells, lib.oracle_fof_brute,
+                  lib.oracle_fof_cells, lib.oracle_num_threads):
+            f.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t)) if a is not None else None
+
+
+def num_threads(n: int = 0) -> int:
+    """Set (n > 0) and return the OpenMP thread count the oracle uses."""
+    return _load().oracle_num_threads(int(n))
+
+
+# ------------------------------------------------------------------ kNN
+
+def _knn(fn, xyz, k, periodic_L, queries, threads):
+    x = np.ascontiguousarray(xyz, dtype=np.float32)
+    n = x.shape[0]
+    q = None if queries is None else np.ascontiguousarray(queries, dtype=np.int64)
+    nq = n if q is None else q.shape[0]
+    idx = np.empty((nq, k), dtype=np.int32)
+    d2 = np.empty((nq, k), dtype=np.float64)
+    rc = fn(_ptr(x, ctypes.c_float), n, int(k), float(periodic_L), _ptr(q, ctypes.c_int64), nq,
+            _ptr(idx, ctypes.c_int32), _ptr(d2, ctypes.c_double), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle kNN failed (rc={rc})")
+    return idx, d2
+
+
+def knn_brute(xyz, k, periodic_L=0.0, queries=None, threads=0):
+    """All-pairs exact kNN (Sec. III): rows ascending by (float64 d2, index), self included."""
+    return _knn(_load().oracle_knn_brute, xyz, k, periodic_L, queries, threads)
+
+
+def knn_cells(xyz, k, periodic_L=0.0, queries=None, threads=0):
+    """Same result as ``knn_brute`` via an exact cell-list search (large N)."""
+    return _knn(_load().oracle_knn_cells, xyz, k, periodic_L, queries, threads)
+
+
+# ------------------------------------------------------------------ FoF
+
+def link_b2(b: float, rel: float = 0.0) -> float:
+    """float64 squared linking length from the float32 argument b, scaled by (1+rel)."""
+    b64 = float(np.float32(b))
+    return b64 * b64 * (1.0 + rel)
+
+
+def fof_brute(xyz, b, periodic_L=0.0, rel=0.0):
+    """All-pairs FoF (Sec. IV): link when d2 <= b^2; label = smallest index in the group."""
+    x = np.ascontiguousarray(xyz, dtype=np.float32)
+    lab = np.empty(x.shape[0], dtype=np.int32)
+    rc = _load().oracle_fof_brute(_ptr(x, ctypes.c_float), x.shape[0], link_b2(b, rel),
+                                  float(periodic_L), _ptr(lab, ctypes.c_int32))
+    if rc != 0:
+        raise ValueError(f"oracle FoF failed (rc={rc})")
+    return lab
+
+
+def fof_cells(xyz, b, periodic_L=0.0, rel=0.0, threads=0):
+    """Same result as ``fof_brute`` via clique cells of side < b/sqrt(3) (large N)."""
+    x = np.ascontiguousarray(xyz, dtype=np.float32)
+    lab = np.empty(x.shape[0], dtype=np.int32)
+    b2 = link_b2(b, rel)
+    rc = _load().oracle_fof_cells(_ptr(x, ctypes.c_float), x.shape[0], float(np.sqrt(b2)), b2,
+                                  float(periodic_L), _ptr(lab, ctypes.c_int32), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle FoF (cells) failed (rc={rc})")
+    return lab
+
+
+def fof_bracket(xyz, b, periodic_L=0.0, rel=1e-6, cells=None):
+    """(labels at b^2(1-rel), labels at b^2(1+rel)): the strict and loose link graphs."""
+    if cells is None:
+        cells = np.asarray(xyz).shape[0] > 20000
+    f = fof_cells if cells else fof_brute
+    return f(xyz, b, periodic_L, -rel), f(xyz, b, periodic_L, rel)
+
+
+# ------------------------------------------------------------------ tree (Sec. II)
+
+KEY_BITS = 21
+SENTINEL_LEVEL = 64
+INDEX_LEVEL_OFFSET = 32
+
+
+def key_box(xyz, periodic_L=0.0):
+    """Quantisation box (lo[3], ext) in float32: [0,L)^3 if periodic, else the
+    bounding box with the largest side as a common extent (1 if degenerate)."""
+    x = np.asarray(xyz, dtype=np.float32)
+    if periodic_L > 0:
+        return np.zeros(3, np.float32), np.float32(periodic_L)
+    lo = x.min(axis=0).astype(np.float32)
+    hi = x.max(axis=0).astype(np.float32)
+    ext = np.float32(np.max(hi - lo))
+    if not ext > 0:
+        ext = np.float32(1.0)
+    return lo, ext
+
+
+def quantise(xyz, periodic_L=0.0):
+    """q_d = min(floor(fl32(fl32(x_d - lo_d) * fl32(2^21 / ext))), 2^21 - 1), all in float32."""
+    x = np.asarray(xyz, dtype=np.float32)
+    lo, ext = key_box(x, periodic_L)
+    scale = np.float32(np.float32(1 << KEY_BITS) / ext)
+    t = (x - lo[None, :]).astype(np.float32)
+    u = (t * scale).astype(np.float32)
+    q = np.floor(u).astype(np.int64)
+    return np.clip(q, 0, (1 << KEY_BITS) - 1).astype(np.uint64)
+
+
+def interleave(q) -> np.ndarray:
+    """Morton key: bit j of q_x -> key bit 3j+2, of q_y -> 3j+1, of q_z -> 3j."""
+    q = np.asarray(q, dtype=np.uint64)
+    key = np.zeros(q.shape[0], dtype=np.uint64)
+    for j in range(KEY_BITS):
+        for d in range(3):
+            bit = (q[:, d] >> np.uint64(j)) & np.uint64(1)
+            key |= bit << np.uint64(3 * j + (2 - d))
+    return key
+
+
+def morton_keys(xyz, periodic_L=0.0):
+    """63-bit z-order keys of float32 points (Sec. II-A, integer Morton key)."""
+    return interleave(quantise(xyz, periodic_L))
+
+
+def zsort(keys):
+    """Stable ascending sort by key: (sorted keys, perm) with perm[i] = original index."""
+    perm = np.argsort(keys, kind="stable").astype(np.int64)
+    return np.asarray(keys)[perm], perm
+
+
+def _bit_length(v: np.ndarray) -> np.ndarray:
+    v = np.asarray(v, dtype=np.uint64)
+    out = np.zeros(v.shape, dtype=np.int64)
+    for s in range(64):
+        out = np.where((v >> np.uint64(s)) != 0, s + 1, out)
+    return out
+
+
+def gap_levels(skeys):
+    """lvl_i for gaps i = 0..N between sorted points i-1 and i (Sec. II-C).
+
+    With integer keys lvl(a, b) is the bit length of a XOR b.  Equal keys are
+    made distinct by appending the sorted position as 32 lower bits, which gives
+    the level bit_length((i-1) XOR i) - 32 (negative).  The gaps before the first
+    and after the last point carry the sentinel level 64 (the paper's -inf/+inf
+    points)."""
+    k = np.asarray(skeys, dtype=np.uint64)
+    n = k.shape[0]
+    lvl = np.full(n + 1, SENTINEL_LEVEL, dtype=np.int64)
+    if n > 1:
+        x = k[:-1] ^ k[1:]
+        i = np.arange(1, n, dtype=np.uint64)
+        idx_lvl = _bit_length((i - np.uint64(1)) ^ i) - INDEX_LEVEL_OFFSET
+        lvl[1:n] = np.where(x != 0, _bit_length(x), idx_lvl)
+    return lvl
+
+
+def node_sizes(skeys, lvl=None):
+    """n_i: number of points in the smallest node holding sorted points i-1 and i.
+
+    A node at level g holds the points whose (extended) key agrees with point i
+    in every bit at or above g; its range [l_b, r_b) is found with searchsorted on
+    the sorted keys (Sec. II-C: binary searches to the left and right)."""
+    k = np.asarray(skeys, dtype=np.uint64)
+    n = k.shape[0]
+    if lvl is None:
+        lvl = gap_levels(k)
+    out = np.full(n + 1, n, dtype=np.int64)
+    if n < 2:
+        return out
+    g = np.asarray(lvl[1:n], dtype=np.int64)
+    i = np.arange(1, n, dtype=np.int64)
+    ki = k[1:n]
+    # distinct-key gaps: the node is the key range sharing every bit >= g
+    sh = np.where(g > 0, g, 0).astype(np.uint64)
+    lo_key = (ki >> sh) << sh
+    hi_key = lo_key | ((np.uint64(1) << sh) - np.uint64(1))
+    lb = np.searchsorted(k, lo_key, side="left")
+    rb = np.searchsorted(k, hi_key, side="right")
+    # equal-key gaps: the aligned block of sorted positions inside the run of equal keys
+    bits = np.where(g > 0, 0, g + INDEX_LEVEL_OFFSET)
+    run_lo = np.searchsorted(k, ki, side="left")
+    run_hi = np.searchsorted(k, ki, side="right")
+    blk = (i >> bits) << bits
+    lb_eq = np.maximum(run_lo, blk)
+    rb_eq = np.minimum(run_hi, blk + (np.int64(1) << bits))
+    out[1:n] = np.where(g > 0, rb - lb, rb_eq - lb_eq)
+    return out
+
+
+def node_sizes_brute(skeys, lvl=None):
+    """n_i by direct counting of the points that share the prefix (O(N^2), tiny N)."""
+    k = [int(v) for v in np.asarray(skeys, dtype=np.uint64)]
+    n = len(k)
+    if lvl is None:
+        lvl = gap_levels(np.asarray(skeys, dtype=np.uint64))
+    out = np.full(n + 1, n, dtype=np.int64)
+    for i in range(1, n):
+        g = int(lvl[i])
+        cnt = 0
+        for j in range(n):
+            if g > 0:
+                same = (k[j] >> g) == (k[i] >> g)
+            else:
+                bits = g + INDEX_LEVEL_OFFSET
+                same = k[j] == k[i] and (j >> bits) == (i >> bits)
+            cnt += same
+        out[i] = cnt
+    return out
+
+
+def num_planes(n: int, nmax0: int = 48, c: int = 8, n_target: int = 1000) -> int:
+    """Number of tree-planes: plane 0 always; plane p >= 1 while the estimated node
+    count N / (N_max^(p) / 2) stays >= N_target (Sec. II-C, eq. N_nodes)."""
+    p = 1
+    while 2 * n >= n_target * nmax0 * c ** p:
+        p += 1
+    return p
+
+
+def plane_splits(skeys, nmax0: int = 48, c: int = 8, n_target: int = 1000, n_planes=None):
+    """Tree-plane splits (Sec. II-C, Fig. tree_construction).
+
+    Returns (spl, gaps): spl[p] holds the splits of plane p -- point indices for
+    p = 0 and indices into plane p-1's node array for p >= 1 -- and gaps[p] the
+    point-space gap index of every split.  A gap is a split of plane p when its
+    n exceeds N_max^(p) = N_max^(0) c^p; the first and last gap always are."""
+    k = np.asarray(skeys, dtype=np.uint64)
+    n = k.shape[0]
+    nsz = node_sizes(k)
+    if n_planes is None:
+        n_planes = num_planes(n, nmax0, c, n_target)
+    gaps = []
+    spl = []
+    cand = np.arange(n + 1)
+    for p in range(n_planes):
+        nmax = nmax0 * c ** p
+        keep = nsz[cand] > nmax
+        keep[0] = True
+        keep[-1] = True
+        pos = np.nonzero(keep)[0]
+        spl.append(pos.astype(np.int64))
+        cand = cand[pos]
+        gaps.append(cand.astype(np.int64))
+    return spl, gaps
+
+
+def plane_nodes(sxyz, gaps):
+    """Per plane: (count[n_nodes], lo[n_nodes,3], hi[n_nodes,3]) of the sorted points."""
+    x = np.asarray(sxyz, dtype=np.float32)
+    out = []
+    for g in gaps:
+        cnt = np.diff(g)
+        lo = np.stack([x[a:b].min(axis=0) for a, b in zip(g[:-1], g[1:])]) if len(cnt) else np.zeros((0, 3), np.float32)
+        hi = np.stack([x[a:b].max(axis=0) for a, b in zip(g[:-1], g[1:])]) if len(cnt) else np.zeros((0, 3), np.float32)
+        out.append((cnt.astype(np.int64), lo.astype(np.float32), hi.astype(np.float32)))
+    return out
+
+
+def canonical_labels(labels) -> np.ndarray:
+    """Relabel a partition so that each group carries its smallest member index."""
+    lab = np.asarray(labels)
+    n = lab.shape[0]
+    first = {}
+    out = np.empty(n, dtype=np.int32)
+    for i in range(n):
+        v = int(lab[i])
+        if v not in first:
+            first[v] = i
+        out[i] = first[v]
+    return out

@@ -1,0 +1,372 @@
+"""Pins for the oracle: each test checks it against something other than itself
+(the paper's worked example, closed forms, an independent enumeration, a
+library routine, or an invariance of the definition)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests import parity
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.startswith("#") or ":" not in line:
+                continue
+            k, v = line.split(":", 1)
+            out[k.strip()] = v.split()
+    return out
+
+
+# ------------------------------------------------------------------ tree: worked example
+
+def test_worked_example_1d():
+    """Fig. tree_construction (Sec. II-C): levels, n, spl^(0), spl^(1)."""
+    g = _golden("worked_example.txt")
+    x = np.array([float(v) for v in g["x"]])
+    keys = np.floor(x * 8).astype(np.uint64)
+    assert keys.tolist() == [int(v) for v in g["fixed_keys"]]
+    lvl = oracle.gap_levels(keys)
+    assert lvl.tolist() == [int(v) for v in g["key_levels"]]
+    paper = [int(v) for v in g["paper_levels_inner"]]
+    assert (lvl[1:-1] - 3).tolist() == paper
+    n = oracle.node_sizes(keys)
+    assert n.tolist() == [int(v) for v in g["n"]]
+    assert oracle.node_sizes_brute(keys).tolist() == n.tolist()
+    spl, _ = oracle.plane_splits(keys, nmax0=int(g["nmax0"][0]), c=int(g["c"][0]), n_planes=2)
+    assert spl[0].tolist() == [int(v) for v in g["spl0"]]
+    assert spl[1].tolist() == [int(v) for v in g["spl1"]]
+
+
+def test_worked_example_3d_on_x_axis():
+    """Same example through the 3-D quantiser: points on the x axis of a periodic box
+    of side 2^18 quantise to q_x = floor(8x); levels scale by 3, n and splits match."""
+    g = _golden("worked_example.txt")
+    x = np.array([float(v) for v in g["x"]], dtype=np.float32)
+    pts = np.zeros((8, 3), np.float32)
+    pts[:, 0] = x
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(8)
+    keys = oracle.morton_keys(pts[perm], periodic_L=float(1 << 18))
+    sk, order = oracle.zsort(keys)
+    assert np.array_equal(perm[order], np.arange(8))
+    lvl = oracle.gap_levels(sk)
+    assert (lvl[1:-1] // 3).tolist() == [int(v) for v in g["key_levels"]][1:-1]
+    assert oracle.node_sizes(sk).tolist() == [int(v) for v in g["n"]]
+    spl, _ = oracle.plane_splits(sk, nmax0=2, c=2, n_planes=2)
+    assert spl[0].tolist() == [int(v) for v in g["spl0"]]
+    assert spl[1].tolist() == [int(v) for v in g["spl1"]]
+
+
+# ------------------------------------------------------------------ tree: keys and order
+
+def test_interleave_bits():
+    q = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [2, 0, 0], [(1 << 21) - 1] * 3, [5, 3, 6]], np.uint64)
+    k = oracle.interleave(q)
+    assert k[0] == 4 and k[1] == 2 and k[2] == 1 and k[3] == 32
+    assert k[4] == (1 << 63) - 1
+    # 5 = 101, 3 = 011, 6 = 110 -> triples (x,y,z) per bit j: j0 (1,1,0) j1 (0,1,1) j2 (1,0,1)
+    assert int(k[5]) == (0b110) | (0b011 << 3) | (0b101 << 6)
+
+
+def _msb_int(a, b):
+    x = a ^ b
+    return x.bit_length() - 1 if x else -1
+
+
+def test_key_order_matches_paper_comparator():
+    """Sorting by the interleaved key equals sorting with the paper's comparator
+    (Sec. II-A): compare along the dimension with the highest differing bit, the
+    first such dimension winning ties (x most significant)."""
+    import functools
+    rng = np.random.default_rng(3)
+    q = rng.integers(0, 1 << 21, size=(300, 3)).astype(np.uint64)
+    q[::7] = q[3]  # duplicates
+    q[::11, 1] = q[5, 1]
+
+    def cmp(a, b):
+        m = [_msb_int(int(a[d]), int(b[d])) for d in range(3)]
+        kd = int(np.argmax(m))
+        if m[kd] < 0:
+            return 0
+        return -1 if int(a[kd]) < int(b[kd]) else 1
+
+    order_cmp = sorted(range(len(q)), key=functools.cmp_to_key(lambda i, j: cmp(q[i], q[j]) or (i - j)))
+    keys = oracle.interleave(q)
+    _, order_key = oracle.zsort(keys)
+    assert order_key.tolist() == order_cmp
+
+
+def test_quantise_periodic_unit_box_exact():
+    x = workloads.uniform(1000, 7)
+    q = oracle.quantise(x, 1.0)
+    assert np.array_equal(q, np.floor(x.astype(np.float64) * (1 << 21)).astype(np.uint64))
+
+
+def test_quantise_open_box_covers_range():
+    x = workloads.uniform(1000, 8) * np.float32(0.5) + np.float32(0.25)
+    q = oracle.quantise(x, 0.0)
+    assert q.min() == 0 and q.max() == (1 << 21) - 1
+
+
+def test_node_sizes_with_duplicate_keys():
+    rng = np.random.default_rng(11)
+    keys = np.sort(rng.integers(0, 40, 300).astype(np.uint64))  # long equal runs
+    lvl = oracle.gap_levels(keys)
+    assert lvl[0] == 64 and lvl[-1] == 64
+    assert ((lvl[1:-1] >= -31) & (lvl[1:-1] <= 63) & (lvl[1:-1] != 0)).all()
+    assert np.array_equal(oracle.node_sizes(keys, lvl), oracle.node_sizes_brute(keys, lvl))
+
+
+@pytest.mark.parametrize("nmax0,c", [(48, 8), (32, 8), (4, 2)])
+def test_plane_invariants(nmax0, c):
+    """Sec. II-C: every plane partitions the points, nodes hold <= N_max^(p) points,
+    coarser splits are a subset of finer ones, and every split has n > N_max^(p)."""
+    x = workloads.clustered(20000, 5, n_blobs=20)
+    x[100:400] = x[100]  # a run of 300 identical points
+    keys = oracle.morton_keys(x, 1.0)
+    sk, _ = oracle.zsort(keys)
+    n = oracle.node_sizes(sk)
+    spl, gaps = oracle.plane_splits(sk, nmax0=nmax0, c=c, n_target=10)
+    assert len(spl) == oracle.num_planes(20000, nmax0, c, 10)
+    for p, (s, g) in enumerate(zip(spl, gaps)):
+        nmax = nmax0 * c ** p
+        assert g[0] == 0 and g[-1] == len(x)
+        assert (np.diff(g) > 0).all()
+        assert (np.diff(g) <= nmax).all()
+        assert (n[g[1:-1]] > nmax).all()
+        if p > 0:
+            assert np.isin(g, gaps[p - 1]).all()
+            assert np.array_equal(gaps[p - 1][s], g)
+
+
+def test_num_planes_large():
+    assert oracle.num_planes(1 << 27, 48, 8, 1000) == 5
+    assert oracle.num_planes(32768, 48, 8, 1000) == 1
+
+
+# ------------------------------------------------------------------ kNN
+
+def _knn_full_sort(x, k, L):
+    """Independent enumeration: the complete distance matrix sorted by (d2, j)."""
+    xd = x.astype(np.float64)
+    d = xd[None, :, :] - xd[:, None, :]
+    if L > 0:
+        d = d - L * np.round(d / L)
+    d2 = (d * d).sum(-1)
+    n = len(x)
+    idx = np.empty((n, k), np.int64)
+    for i in range(n):
+        o = np.lexsort((np.arange(n), d2[i]))
+        idx[i] = o[:k]
+    return idx, np.take_along_axis(d2, idx, 1)
+
+
+@pytest.mark.parametrize("L", [0.0, 1.0])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_knn_brute_vs_full_sort(L, seed):
+    x = workloads.uniform(64, 100 + seed)
+    x[5] = x[9]  # an exact duplicate
+    for k in (1, 5, 16, 64):
+        ii, dd = oracle.knn_brute(x, k, L)
+        ri, rd = _knn_full_sort(x, k, L)
+        assert np.array_equal(ii, ri)
+        assert np.array_equal(dd, rd)
+
+
+def test_knn_brute_vs_scipy():
+    from scipy.spatial import cKDTree
+    x = workloads.uniform(2000, 5)
+    for L in (0.0, 1.0):
+        ii, dd = oracle.knn_brute(x, 12, L)
+        t = cKDTree(x.astype(np.float64), boxsize=1.0 if L > 0 else None)
+        sd, si = t.query(x.astype(np.float64), k=12)
+        assert np.allclose(dd, sd ** 2, rtol=1e-12, atol=0)
+        # continuous random data: no ties, so the index sets agree too
+        assert np.array_equal(np.sort(ii, 1), np.sort(si, 1))
+
+
+def test_knn_lattice_closed_form():
+    """Interior point of a cubic lattice: self, then 6 at h^2, 12 at 2h^2, 8 at 3h^2;
+    k = 16 takes 9 of the 12 second neighbours, chosen by lowest index."""
+    m = 7
+    x = workloads.lattice(m, spacing_bits=9)
+    h2 = (1.0 / 512) ** 2
+    c = (3 * m + 3) * m + 3
+    ii, dd = oracle.knn_brute(x, 27, 0.0, queries=[c])
+    assert ii[0, 0] == c and dd[0, 0] == 0
+    assert np.allclose(dd[0, 1:7], h2) and np.allclose(dd[0, 7:19], 2 * h2) and np.allclose(dd[0, 19:27], 3 * h2)
+    # the expected 12 second neighbours, in index order
+    second = sorted(((3 + a) * m + 3 + b) * m + 3 + e for a in (-1, 0, 1) for b in (-1, 0, 1) for e in (-1, 0, 1)
+                    if abs(a) + abs(b) + abs(e) == 2)
+    assert ii[0, 7:19].tolist() == second
+    i16, _ = oracle.knn_brute(x, 16, 0.0, queries=[c])
+    assert i16[0, 7:16].tolist() == second[:9]
+
+
+def test_knn_periodic_lattice_wraps():
+    """On a periodic lattice every point sees 6 neighbours at h^2, including across the box edge."""
+    x = workloads.lattice(8, spacing_bits=3)  # spacing 1/8 fills the unit box
+    ii, dd = oracle.knn_brute(x, 7, 1.0)
+    assert np.allclose(dd[:, 1:], (1.0 / 8) ** 2)
+    ii_open, dd_open = oracle.knn_brute(x, 7, 0.0)
+    assert dd_open[0, 6] > (1.0 / 8) ** 2  # a corner has only 3 nearest neighbours when open
+
+
+def test_knn_permutation_and_translation_invariance():
+    x = workloads.clustered(3000, 9, n_blobs=10)
+    k = 10
+    ii, dd = oracle.knn_brute(x, k, 1.0)
+    perm = np.random.default_rng(1).permutation(len(x))
+    ip, dp = oracle.knn_brute(x[perm], k, 1.0)
+    assert np.array_equal(dd[perm], dp)
+    shift = np.array([12345, 999, 777777], np.float64) / (1 << 24)
+    xs = workloads.snap_unit(x.astype(np.float64) + shift)
+    it, dt = oracle.knn_brute(xs, k, 1.0)
+    assert np.array_equal(dt, dd)
+    assert (np.diff(dd, axis=1) >= 0).all()
+
+
+@pytest.mark.parametrize("L", [0.0, 1.0])
+@pytest.mark.parametrize("gen", ["uniform", "clustered"])
+def test_knn_cells_equals_brute(L, gen):
+    x = workloads.uniform(6000, 21) if gen == "uniform" else workloads.clustered(6000, 22, n_blobs=8)
+    x[10:20] = x[10]
+    for k in (1, 16, 32):
+        a = oracle.knn_brute(x, k, L)
+        b = oracle.knn_cells(x, k, L)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# ------------------------------------------------------------------ FoF
+
+def _fof_warshall(x, b2, L):
+    """Independent enumeration: boolean transitive closure of the link matrix."""
+    xd = x.astype(np.float64)
+    d = xd[None, :, :] - xd[:, None, :]
+    if L > 0:
+        d = d - L * np.round(d / L)
+    adj = (d * d).sum(-1) <= b2
+    n = len(x)
+    r = adj.copy()
+    for m in range(n):
+        r |= r[:, m:m + 1] & r[m:m + 1, :]
+    return np.array([int(np.argmax(r[i])) for i in range(n)], np.int32)
+
+
+@pytest.mark.parametrize("L", [0.0, 1.0])
+def test_fof_brute_vs_warshall(L):
+    for seed in range(3):
+        x = workloads.uniform(60, 200 + seed)
+        for b in (0.05, 0.12, 0.2):
+            lab = oracle.fof_brute(x, b, L)
+            assert np.array_equal(lab, _fof_warshall(x, oracle.link_b2(b), L))
+
+
+def test_fof_brute_vs_scipy():
+    from scipy.sparse.csgraph import connected_components
+    from scipy.spatial import cKDTree
+    x = workloads.clustered(5000, 3, n_blobs=30)
+    b = 0.01
+    for L in (0.0, 1.0):
+        lab = oracle.fof_brute(x, b, L)
+        t = cKDTree(x.astype(np.float64), boxsize=1.0 if L > 0 else None)
+        pairs = t.query_pairs(float(np.float32(b)), output_type="ndarray")
+        import scipy.sparse as sp
+        g = sp.coo_matrix((np.ones(len(pairs)), (pairs[:, 0], pairs[:, 1])), shape=(len(x),) * 2)
+        _, cc = connected_components(g, directed=False)
+        assert np.array_equal(oracle.canonical_labels(cc), lab)
+
+
+def test_fof_lattice_closed_form():
+    """Cubic lattice of spacing h: b < h gives singletons, b = h (<= is the linking
+    rule, Sec. IV-A) and h < b < sqrt(2) h give one group; periodic too; removing one
+    plane of the open lattice splits it in two."""
+    m = 6
+    h = 1.0 / 512
+    x = workloads.lattice(m, spacing_bits=9)
+    n = len(x)
+    assert np.array_equal(oracle.fof_brute(x, 0.999 * h), np.arange(n))
+    for b in (h, 1.001 * h, 1.4 * h):
+        assert (oracle.fof_brute(x, b) == 0).all()
+    xp = workloads.lattice(8, spacing_bits=3)
+    assert (oracle.fof_brute(xp, 1.0 / 8, 1.0) == 0).all()
+    assert np.array_equal(oracle.fof_brute(xp, 0.99 / 8, 1.0), np.arange(len(xp)))
+    ii = np.indices((m, m, m)).reshape(3, -1).T
+    keep = ii[:, 0] != 2
+    lab = oracle.fof_brute(x[keep], h)
+    assert len(np.unique(lab)) == 2
+    # the periodic lattice minus one plane stays connected through the wrap
+    iip = np.indices((8, 8, 8)).reshape(3, -1).T
+    labp = oracle.fof_brute(xp[iip[:, 0] != 2], 1.0 / 8, 1.0)
+    assert len(np.unique(labp)) == 1
+
+
+def test_fof_symmetry_and_permutation_invariance():
+    x = workloads.clustered(2000, 13, n_blobs=12)
+    b = 0.02
+    lab = oracle.fof_brute(x, b, 1.0)
+    parity.check_canonical(lab)
+    perm = np.random.default_rng(4).permutation(len(x))
+    labp = oracle.fof_brute(x[perm], b, 1.0)
+    # same partition: relabel through the permutation
+    assert np.array_equal(oracle.canonical_labels(lab[perm]), labp)
+    # linking is symmetric: reversing every pair's order gives the same partition
+    xr = x[::-1].copy()
+    assert np.array_equal(oracle.canonical_labels(lab[::-1]), oracle.fof_brute(xr, b, 1.0))
+
+
+@pytest.mark.parametrize("L", [0.0, 1.0])
+@pytest.mark.parametrize("gen", ["uniform", "clustered"])
+def test_fof_cells_equals_brute(L, gen):
+    n = 8000
+    x = workloads.uniform(n, 31) if gen == "uniform" else workloads.clustered(n, 32, n_blobs=8)
+    x[50:90] = x[50]
+    for fac in (0.2, 0.5, 1.0):
+        b = fac * workloads.mean_spacing(n)
+        assert np.array_equal(oracle.fof_cells(x, b, L), oracle.fof_brute(x, b, L))
+    # a large linking length relative to the box (many cells per neighbourhood)
+    assert np.array_equal(oracle.fof_cells(x[:500], 0.3, L), oracle.fof_brute(x[:500], 0.3, L))
+
+
+# ------------------------------------------------------------------ comparison rules
+
+def test_knn_rule_rejects_wrong_and_accepts_ties():
+    x = workloads.lattice(5, spacing_bits=9)
+    q = np.array([62])
+    ri, rd = oracle.knn_brute(x, 8, 0.0, queries=q)
+    gd = rd.astype(np.float32)
+    parity.check_knn(x, q, ri, gd, ri, rd)
+    # swapping two tied neighbours (both at h^2) is accepted
+    gi = ri.copy()
+    gi[0, 1], gi[0, 2] = gi[0, 2], gi[0, 1]
+    parity.check_knn(x, q, gi, gd, ri, rd)
+    # replacing a neighbour by a farther point is rejected
+    gi = ri.copy()
+    gi[0, 7] = 0
+    with pytest.raises(AssertionError):
+        parity.check_knn(x, q, gi, gd, ri, rd)
+    # a d2 off by more than 2 ulp is rejected
+    bad = gd.copy()
+    bad[0, 3] = np.nextafter(np.nextafter(np.nextafter(bad[0, 3], 1), 1), 1)
+    with pytest.raises(AssertionError):
+        parity.check_knn(x, q, ri, bad, ri, rd)
+
+
+def test_fof_rule():
+    x = workloads.uniform(500, 3)
+    b = 0.08
+    s, lo = oracle.fof_bracket(x, b)
+    lab = oracle.fof_brute(x, b)
+    parity.check_fof(lab, s, lo)
+    wrong = lab.copy()
+    wrong[wrong == wrong[7]] = 7 if wrong[7] != 7 else wrong[7]
+    wrong[123] = 0 if lab[123] != 0 else 1
+    with pytest.raises(AssertionError):
+        parity.check_fof(wrong, s, lo)
