@@ -1,0 +1,154 @@
+/*
+ * jzt.h -- C ABI of the GB300 (sm_103a) jz-tree hot path: exact k-nearest
+ * neighbours and friends-of-friends (FoF) groups of 3-D float32 points via a
+ * Morton-ordered plane-based tree and a dual tree walk.
+ *
+ * The method is that of "jz-tree: GPU friendly neighbour search and
+ * friends-of-friends with dual tree walks in JAX plus CUDA" (Stuecker, Hahn,
+ * Winkler, Gutierrez Adame, Floess; arXiv 2604.05885).  Section references
+ * below are to that paper.
+ *
+ * Conventions for every call:
+ *   - Pointers prefixed d_ are DEVICE pointers (cudaMalloc / torch CUDA
+ *     storage) on the current device; all others are host pointers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All device work is enqueued on it; no call synchronises the
+ *     stream unless its comment says so.
+ *   - No call allocates device memory.  The caller provides a workspace of at
+ *     least jzt_workspace_bytes() bytes (256-byte aligned) and owns it, the
+ *     inputs and the outputs.  The library owns only jzt_tree host handles.
+ *   - Return codes: JZT_OK on success, else a negative jzt_error value; the
+ *     thread-local jzt_last_error() string describes it.  Argument errors are
+ *     detected synchronously.  Errors that depend on the data (capacity
+ *     overflow, invalid coordinates, exhausted waits) are recorded in a
+ *     status word inside the workspace and read with jzt_status().
+ *   - Sizes: 1 <= N < 2^30 points.  xyz is N x 3 row-major float32 (x,y,z per
+ *     point), 4-byte aligned (16-byte aligned takes the vector-load path).
+ *   - periodic_L > 0 selects a periodic box [0,L)^3 with minimum-image
+ *     distances (Sec. III-G); every coordinate must lie in [0,L).
+ *     periodic_L <= 0 selects open boundaries.
+ */
+#ifndef JZT_H
+#define JZT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum jzt_error {
+    JZT_OK = 0,
+    JZT_ERR_INVALID = -1,      /* bad argument (N, k, b, L, null pointer, alignment) */
+    JZT_ERR_UNSUPPORTED = -2,  /* valid but not implemented here (k > 32) */
+    JZT_ERR_CUDA = -3,         /* a CUDA runtime call failed (message in jzt_last_error) */
+    JZT_ERR_WORKSPACE = -4,    /* ws_bytes below jzt_workspace_bytes() */
+    JZT_ERR_CAPACITY = -5,     /* device: node or interaction-list capacity exceeded */
+    JZT_ERR_INPUT = -6,        /* device: NaN/Inf coordinate, or outside [0,L) when periodic */
+    JZT_ERR_TIMEOUT = -7       /* device: a bounded wait or CAS retry loop gave up */
+} jzt_error;
+
+/* Tree and walk parameters; a zero field takes the default shown. */
+typedef struct jzt_params {
+    int32_t nmax0;            /* N_max^(0): leaf capacity, 1..32 (default 32; Sec. II-C) */
+    int32_t plane_factor;     /* c in N_max^(p) = N_max^(0) c^p (default 8; Sec. II-C) */
+    int32_t n_target;         /* coarsening stops below N_target estimated nodes (default 1000) */
+    int32_t ngr;              /* NGR: top nodes per super node (default 32; Alg. 1) */
+    float alloc_fac_nodes;    /* node capacity per plane = fac * N / (N_max^(p)/2) (default 2; Eq. alloc_nodes) */
+    float alloc_fac_ilist;    /* interaction-list capacity = fac * N / (N_max^(0)/2) (default 128; Eq. alloc_ilist) */
+    int32_t heap_size;        /* N_r: entries of the FindRmax register heap, 2..16 (default 8; Alg. 3) */
+    int32_t reserved[7];      /* must be zero */
+} jzt_params;
+
+typedef struct jzt_tree jzt_tree;  /* opaque; lives on the host, points into the workspace */
+
+/* Status block read back by jzt_status. */
+typedef struct jzt_status_info {
+    int32_t code;             /* jzt_error of the first device-side failure, JZT_OK if none */
+    int32_t detail;           /* which stage failed (implementation-defined, for messages) */
+    int64_t required_bytes;   /* JZT_ERR_CAPACITY: a workspace size that is at least needed
+                                 (a lower bound: later stages may need more) */
+    int64_t ilist_entries;    /* interaction-list entries used by the last walk */
+    int32_t n_planes;         /* tree-planes built (Sec. II-C) */
+    int32_t reserved;
+    int64_t n_nodes[16];      /* nodes per plane, plane 0 = leaves */
+} jzt_status_info;
+
+/* Workspace size for N points and parameters p (NULL = defaults).  k_or_0 is the
+ * largest k the caller will ask for (0 if only FoF); it does not change the size
+ * in this version but is validated (1..32).  Host-only, no CUDA call.
+ * Errors: JZT_ERR_INVALID for N out of range, bad parameters or null `bytes`. */
+int jzt_workspace_bytes(int64_t n, int k_or_0, const jzt_params *p, size_t *bytes);
+
+/* Build the tree of Sec. II on the device: domain (bounding box when open),
+ * 3 x 21-bit Morton keys with x most significant (Sec. II-A), stable LSD radix
+ * sort of (key, index), gather of the sorted points, gap levels and tree-plane
+ * splits (Sec. II-C; N_max^(p) = N_max^(0) c^p), per-node counts and bounding
+ * boxes.  d_xyz is read during this call's stream work only: the tree keeps its
+ * own sorted copy in the workspace.  *out receives a host handle that stays valid
+ * until jzt_tree_free; the workspace must outlive it and must not be reused by
+ * another build meanwhile.  Asynchronous; device-side failures go to the status. */
+int jzt_build(const float *d_xyz, int64_t n, float periodic_L, const jzt_params *p,
+              void *d_ws, size_t ws_bytes, void *stream, jzt_tree **out);
+
+/* Exact k nearest neighbours of every point among all points, the point itself
+ * included (Sec. III, Alg. 1-3: dense super-node interaction list, NodeToNode per
+ * plane, LeafToLeaf).  Row i of d_idx / d_dist2 (N x k, row-major) lists point i's
+ * neighbours by original index, ascending by (float32 squared distance, index).
+ * order: 0 = rows in input order (Sec. III-E final reordering), 1 = rows in z order
+ * (row r belongs to the point at sorted position r, whose original index is the
+ * .w lane of jzt_tree_arrays' pts).
+ * Errors: JZT_ERR_INVALID (k < 1, k > N, null outputs), JZT_ERR_UNSUPPORTED (k > 32). */
+int jzt_tree_knn(jzt_tree *t, int k, int order, int32_t *d_idx, float *d_dist2, void *stream);
+
+/* FoF groups at linking length b (Sec. IV): points i, j are friends when their
+ * float32 squared distance is <= b*b (float32); groups are the connected
+ * components.  d_labels[i] (N int32, input order) = smallest original index in
+ * point i's group.  Whole-node links when the node-node upper distance is <= b
+ * (Sec. IV-A).  Errors: JZT_ERR_INVALID (b <= 0 or not finite, periodic b >= L/2). */
+int jzt_tree_fof(jzt_tree *t, float b, int32_t *d_labels, void *stream);
+
+/* One-call forms: build, then walk, on the same workspace. */
+int jzt_knn(const float *d_xyz, int64_t n, int k, float periodic_L,
+            int32_t *d_idx, float *d_dist2, void *d_ws, size_t ws_bytes, void *stream);
+int jzt_fof(const float *d_xyz, int64_t n, float b, float periodic_L,
+            int32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream);
+
+/* Synchronises `stream`, then reads the status block of workspace d_ws into *info
+ * (may be NULL) and returns its code (JZT_OK or a device-side jzt_error).
+ * Returns JZT_ERR_CUDA if the synchronisation itself fails. */
+int jzt_status(const void *d_ws, void *stream, jzt_status_info *info);
+
+/* Device pointers into the tree (valid while the tree lives):
+ *   keys  -- N uint64 Morton keys, sorted ascending
+ *   pts   -- N float4 sorted points (x, y, z, and in .w the original index of
+ *            the point as int32 bits)
+ * and the number of planes.  Host-only, no CUDA call. */
+int jzt_tree_arrays(const jzt_tree *t, const uint64_t **d_keys, const float **d_pts,
+                    int32_t *n_planes);
+
+/* Copies plane p of the tree to HOST buffers (synchronises `stream`):
+ *   spl   -- n_nodes+1 int32 splits: point indices for p = 0, indices into plane
+ *            p-1's nodes for p >= 1 (Sec. II-C, Fig. tree_construction)
+ *   count -- n_nodes int32 points per node
+ *   box   -- n_nodes x 6 float32 bounding boxes (lo x,y,z, hi x,y,z)
+ * Any of spl/count/box may be NULL.  cap is the capacity (in nodes) of the
+ * caller's buffers; *n_nodes receives the node count.
+ * Errors: JZT_ERR_INVALID (p out of range, cap too small). */
+int jzt_tree_plane(const jzt_tree *t, int p, int64_t cap, int64_t *n_nodes,
+                   int32_t *spl, int32_t *count, float *box, void *stream);
+
+void jzt_tree_free(jzt_tree *t);
+
+/* Thread-local description of the last error returned on this thread. */
+const char *jzt_last_error(void);
+
+/* Library version string. */
+const char *jzt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JZT_H */

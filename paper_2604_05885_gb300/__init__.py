@@ -1,0 +1,250 @@
+"""Python binding of libjzt.so: exact kNN and FoF on GB300 (sm_103a).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libjzt.so behind the C ABI declared in include/jzt.h.  PyTorch
+provides device memory (workspace and outputs) and the current stream.
+
+The functions mirror the C entry points:
+
+* ``workspace_bytes(n, k=0, params=None)``
+* ``build(xyz, periodic_L=0.0, params=None, workspace=None) -> Tree``
+* ``Tree.knn(k, order=0) -> (idx int32 [N,k], dist2 float32 [N,k])``
+* ``Tree.fof(b) -> labels int32 [N]``
+* ``knn(xyz, k, periodic_L=0.0)`` / ``fof(xyz, b, periodic_L=0.0)`` one-call forms
+* ``status(workspace) -> dict``
+
+A missing or unloadable library raises at import time: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libjzt.so")
+
+JZT_OK = 0
+JZT_ERR_INVALID = -1
+JZT_ERR_UNSUPPORTED = -2
+JZT_ERR_CUDA = -3
+JZT_ERR_WORKSPACE = -4
+JZT_ERR_CAPACITY = -5
+JZT_ERR_INPUT = -6
+JZT_ERR_TIMEOUT = -7
+_NAMES = {0: "ok", -1: "invalid", -2: "unsupported", -3: "cuda", -4: "workspace",
+          -5: "capacity", -6: "input", -7: "timeout"}
+
+# Every entry point declared in include/jzt.h.
+SYMBOLS = ("jzt_workspace_bytes", "jzt_build", "jzt_tree_knn", "jzt_tree_fof", "jzt_knn", "jzt_fof",
+           "jzt_status", "jzt_tree_arrays", "jzt_tree_plane", "jzt_tree_free", "jzt_last_error",
+           "jzt_version")
+
+
+class JztError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    """Mirror of jzt_params (zero fields take the library defaults)."""
+    _fields_ = [("nmax0", ctypes.c_int32), ("plane_factor", ctypes.c_int32),
+                ("n_target", ctypes.c_int32), ("ngr", ctypes.c_int32),
+                ("alloc_fac_nodes", ctypes.c_float), ("alloc_fac_ilist", ctypes.c_float),
+                ("heap_size", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class StatusInfo(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_int32), ("detail", ctypes.c_int32),
+                ("required_bytes", ctypes.c_int64), ("ilist_entries", ctypes.c_int64),
+                ("n_planes", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_nodes", ctypes.c_int64 * 16)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, f32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_size_t
+    lib.jzt_workspace_bytes.argtypes = [i64, ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(sz)]
+    lib.jzt_build.argtypes = [vp, i64, f32, ctypes.POINTER(Params), vp, sz, vp, ctypes.POINTER(vp)]
+    lib.jzt_tree_knn.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+    lib.jzt_tree_fof.argtypes = [vp, f32, vp, vp]
+    lib.jzt_knn.argtypes = [vp, i64, ctypes.c_int, f32, vp, vp, vp, sz, vp]
+    lib.jzt_fof.argtypes = [vp, i64, f32, f32, vp, vp, sz, vp]
+    lib.jzt_status.argtypes = [vp, vp, ctypes.POINTER(StatusInfo)]
+    lib.jzt_tree_arrays.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32)]
+    lib.jzt_tree_plane.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(i64), vp, vp, vp, vp]
+    lib.jzt_tree_free.argtypes = [vp]
+    lib.jzt_tree_free.restype = None
+    lib.jzt_last_error.restype = ctypes.c_char_p
+    lib.jzt_version.restype = ctypes.c_char_p
+    for name in ("jzt_workspace_bytes", "jzt_build", "jzt_tree_knn", "jzt_tree_fof", "jzt_knn",
+                 "jzt_fof", "jzt_status", "jzt_tree_arrays", "jzt_tree_plane"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def version() -> str:
+    return lib.jzt_version().decode()
+
+
+def _check(rc: int):
+    if rc != JZT_OK:
+        raise JztError(rc, lib.jzt_last_error().decode())
+
+
+def _params(params) -> ctypes.POINTER(Params) | None:
+    if params is None:
+        return None
+    if isinstance(params, Params):
+        return ctypes.pointer(params)
+    p = Params()
+    for k, v in dict(params).items():
+        setattr(p, k, v)
+    return ctypes.pointer(p)
+
+
+def _stream(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def workspace_bytes(n: int, k: int = 0, params=None) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib.jzt_workspace_bytes(int(n), int(k), _params(params), ctypes.byref(out)))
+    return int(out.value)
+
+
+def alloc_workspace(n: int, k: int = 0, params=None, device=None) -> torch.Tensor:
+    nb = workspace_bytes(n, k, params)
+    return torch.empty(nb, dtype=torch.uint8, device=device or "cuda")
+
+
+def _check_xyz(xyz: torch.Tensor):
+    if not (isinstance(xyz, torch.Tensor) and xyz.is_cuda and xyz.dtype == torch.float32
+            and xyz.dim() == 2 and xyz.shape[1] == 3 and xyz.is_contiguous()):
+        raise ValueError("xyz must be a contiguous CUDA float32 tensor of shape (N, 3)")
+
+
+def status(workspace: torch.Tensor, stream=None, raise_on_error: bool = False) -> dict:
+    """Synchronise the stream and read the workspace status block."""
+    info = StatusInfo()
+    rc = lib.jzt_status(ctypes.c_void_p(workspace.data_ptr()), ctypes.c_void_p(_stream(stream)),
+                        ctypes.byref(info))
+    if rc == JZT_ERR_CUDA or rc == JZT_ERR_INVALID:
+        _check(rc)
+    out = dict(code=info.code, name=_NAMES.get(info.code, str(info.code)), detail=info.detail,
+               required_bytes=info.required_bytes, ilist_entries=info.ilist_entries,
+               n_planes=info.n_planes, n_nodes=[info.n_nodes[i] for i in range(16)])
+    if raise_on_error and info.code != JZT_OK:
+        raise JztError(info.code, lib.jzt_last_error().decode())
+    return out
+
+
+class Tree:
+    """A tree built in a caller-owned workspace (see jzt_build)."""
+
+    def __init__(self, xyz: torch.Tensor, periodic_L: float = 0.0, params=None,
+                 workspace: torch.Tensor | None = None, stream=None):
+        _check_xyz(xyz)
+        n = xyz.shape[0]
+        self.n = n
+        self.periodic_L = float(periodic_L)
+        self.params = params
+        self.workspace = workspace if workspace is not None else alloc_workspace(n, 0, params, xyz.device)
+        self._h = ctypes.c_void_p(0)
+        _check(lib.jzt_build(ctypes.c_void_p(xyz.data_ptr()), n, self.periodic_L, _params(params),
+                             ctypes.c_void_p(self.workspace.data_ptr()), self.workspace.numel(),
+                             ctypes.c_void_p(_stream(stream)), ctypes.byref(self._h)))
+
+    def knn(self, k: int, order: int = 0, out=None, stream=None):
+        dev = self.workspace.device
+        if out is None:
+            idx = torch.empty((self.n, k), dtype=torch.int32, device=dev)
+            d2 = torch.empty((self.n, k), dtype=torch.float32, device=dev)
+        else:
+            idx, d2 = out
+        _check(lib.jzt_tree_knn(self._h, int(k), int(order), ctypes.c_void_p(idx.data_ptr()),
+                                ctypes.c_void_p(d2.data_ptr()), ctypes.c_void_p(_stream(stream))))
+        return idx, d2
+
+    def fof(self, b: float, out=None, stream=None):
+        lab = out if out is not None else torch.empty(self.n, dtype=torch.int32, device=self.workspace.device)
+        _check(lib.jzt_tree_fof(self._h, float(b), ctypes.c_void_p(lab.data_ptr()),
+                                ctypes.c_void_p(_stream(stream))))
+        return lab
+
+    def arrays(self):
+        """(sorted keys uint64 view as int64 [N], sorted points float32 [N,4], n_planes)."""
+        kp, pp, npl = ctypes.c_void_p(0), ctypes.c_void_p(0), ctypes.c_int32(0)
+        _check(lib.jzt_tree_arrays(self._h, ctypes.byref(kp), ctypes.byref(pp), ctypes.byref(npl)))
+        ws = self.workspace
+        base = ws.data_ptr()
+        koff, poff = kp.value - base, pp.value - base
+        keys = ws[koff:koff + 8 * self.n].view(torch.int64)
+        pts = ws[poff:poff + 16 * self.n].view(torch.float32).view(self.n, 4)
+        return keys, pts, int(npl.value)
+
+    def plane(self, p: int, stream=None):
+        """Host copies of plane p: (spl int32 [n+1], count int32 [n], box float32 [n,6])."""
+        import numpy as np
+        nn = ctypes.c_int64(0)
+        _check(lib.jzt_tree_plane(self._h, int(p), 0, ctypes.byref(nn), None, None, None,
+                                  ctypes.c_void_p(_stream(stream))))
+        n = int(nn.value)
+        spl = np.empty(n + 1, np.int32)
+        cnt = np.empty(max(n, 1), np.int32)
+        box = np.empty((max(n, 1), 6), np.float32)
+        _check(lib.jzt_tree_plane(self._h, int(p), n, ctypes.byref(nn),
+                                  ctypes.c_void_p(spl.ctypes.data), ctypes.c_void_p(cnt.ctypes.data),
+                                  ctypes.c_void_p(box.ctypes.data), ctypes.c_void_p(_stream(stream))))
+        return spl, cnt[:n], box[:n]
+
+    def status(self, stream=None, raise_on_error: bool = False) -> dict:
+        return status(self.workspace, stream, raise_on_error)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.jzt_tree_free(h)
+            self._h = ctypes.c_void_p(0)
+
+
+def build(xyz, periodic_L=0.0, params=None, workspace=None, stream=None) -> Tree:
+    return Tree(xyz, periodic_L, params, workspace, stream)
+
+
+def knn(xyz: torch.Tensor, k: int, periodic_L: float = 0.0, workspace=None, stream=None, check=True):
+    """One-call exact kNN (jzt_knn); returns (idx [N,k] int32, dist2 [N,k] float32)."""
+    _check_xyz(xyz)
+    n = xyz.shape[0]
+    ws = workspace if workspace is not None else alloc_workspace(n, k, None, xyz.device)
+    idx = torch.empty((n, k), dtype=torch.int32, device=xyz.device)
+    d2 = torch.empty((n, k), dtype=torch.float32, device=xyz.device)
+    _check(lib.jzt_knn(ctypes.c_void_p(xyz.data_ptr()), n, int(k), float(periodic_L),
+                       ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
+                       ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(_stream(stream))))
+    if check:
+        status(ws, stream, raise_on_error=True)
+    return idx, d2
+
+
+def fof(xyz: torch.Tensor, b: float, periodic_L: float = 0.0, workspace=None, stream=None, check=True):
+    """One-call FoF (jzt_fof); returns labels [N] int32 (smallest index of each group)."""
+    _check_xyz(xyz)
+    n = xyz.shape[0]
+    ws = workspace if workspace is not None else alloc_workspace(n, 0, None, xyz.device)
+    lab = torch.empty(n, dtype=torch.int32, device=xyz.device)
+    _check(lib.jzt_fof(ctypes.c_void_p(xyz.data_ptr()), n, float(b), float(periodic_L),
+                       ctypes.c_void_p(lab.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                       ctypes.c_void_p(_stream(stream))))
+    if check:
+        status(ws, stream, raise_on_error=True)
+    return lab

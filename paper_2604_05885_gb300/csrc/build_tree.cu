@@ -1,0 +1,848 @@
+// Tree construction on the device (Sec. II): domain, Morton keys, LSD radix
+// sort, gather, gap levels and tree-plane splits, node records.
+//
+// Layout in HBM (all in the caller's workspace):
+//   keys  uint64[N] x2 and vals uint32[N] x2 (radix ping-pong), sorted points
+//   float4[N] (x, y, z, original index bits), per plane: splits int32[n+1],
+//   point-space gap index int32[n+1], node size at each split int32[n+1] and
+//   32-byte node records.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace jzt {
+
+namespace {
+
+constexpr uint32_t kFlagA = 1u << 30;  // look-back: tile aggregate published
+constexpr uint32_t kFlagP = 2u << 30;  // look-back: inclusive prefix published
+constexpr uint32_t kValMask = (1u << 30) - 1;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Inclusive scan within a warp.
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  int lane = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan over a block of NT threads (one value each); returns the
+// exclusive prefix and writes the block total to *total.
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t s_w[NT / 32];
+  __shared__ uint32_t s_tot;
+  uint32_t inc = warp_incl_scan(v);
+  if (lane_id() == 31) s_w[warp_id()] = inc;
+  __syncthreads();
+  if (warp_id() == 0) {
+    uint32_t w = lane_id() < NT / 32 ? s_w[lane_id()] : 0u;
+    uint32_t wi = warp_incl_scan(w);
+    if (lane_id() < NT / 32) s_w[lane_id()] = wi - w;
+    if (lane_id() == 31) s_tot = wi;  // lanes past NT/32 add zero: lane 31 holds the total
+  }
+  __syncthreads();
+  uint32_t res = s_w[warp_id()] + inc - v;
+  *total = s_tot;
+  __syncthreads();  // s_w / s_tot may be reused by the caller's next scan
+  return res;
+}
+
+// Decoupled look-back over tiles with one counter per tile (single-pass chained
+// scan).  Called by one full warp; returns the exclusive prefix of `count` over
+// tiles 0..tile-1 in every lane and publishes this tile's inclusive prefix.
+// Waits are bounded: on exhaustion the status is set to JZT_ERR_TIMEOUT.
+__device__ unsigned long long chained_scan(unsigned long long* st, int64_t tile, uint32_t count,
+                                           Meta* m, int stage) {
+  const unsigned long long A = 1ull << 62, P = 2ull << 62, MASK = (1ull << 62) - 1;
+  const int lane = lane_id();
+  if (tile == 0) {
+    if (lane == 0) st_release_u64(&st[0], P | count);
+    return 0;
+  }
+  if (lane == 0) st_release_u64(&st[tile], A | count);
+  unsigned long long excl = 0;
+  int64_t j = tile - 1;
+  long long spins = 0;
+  while (true) {
+    int64_t t = j - lane;
+    unsigned long long v = (t >= 0) ? ld_acquire_u64(&st[t]) : P;
+    unsigned flag = (unsigned)(v >> 62);
+    unsigned pm = __ballot_sync(0xffffffffu, flag == 2);
+    unsigned nr = __ballot_sync(0xffffffffu, flag == 0);
+    unsigned long long need = pm ? (((unsigned long long)(pm & (0u - pm)) << 1) - 1ull) : 0xffffffffull;
+    if (nr & (unsigned)need) {
+      if (++spins > kSpinLimit || failed(m)) {
+        if (lane == 0) set_error(m, JZT_ERR_TIMEOUT, stage);
+        break;
+      }
+      continue;
+    }
+    unsigned long long val = ((need >> lane) & 1ull) ? (v & MASK) : 0ull;
+    excl += warp_sum(val);
+    if (pm) break;
+    j -= 32;
+  }
+  if (lane == 0) st_release_u64(&st[tile], P | (excl + count));
+  return excl;
+}
+
+// ------------------------------------------------------------------ meta / box
+
+__global__ void k_init_meta(Meta* m, int n_planes) {
+  int t = threadIdx.x;
+  if (t == 0) {
+    m->status = 0;
+    m->detail = 0;
+    m->required_bytes = 0;
+    m->arena_used = 0;
+    m->arena_peak = 0;
+    m->n_planes = n_planes;
+  }
+  if (t < 3) {
+    m->bbox_enc[t] = 0xffffffffu;
+    m->bbox_enc[3 + t] = 0u;
+  }
+  if (t < kMaxPlanes + 1) m->n_nodes[t] = 0;
+  if (t < 32) m->tile_ctr[t] = 0;
+  uint32_t* h = &m->radix_hist[0][0];
+  for (int i = t; i < kRadixPasses * kRadixBins; i += blockDim.x) h[i] = 0;
+}
+
+__global__ void k_zero_u64(unsigned long long* p, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = 0ull;
+}
+
+__device__ __forceinline__ bool bad_coord(float v, float L) {
+  return !isfinite(v) || (L > 0.0f && (v < 0.0f || v >= L));
+}
+
+// Validation of every coordinate and, for open boxes, the bounding box
+// (min/max reduction).  VEC: 16-byte aligned input read as float4 (3 float4 =
+// 4 points).
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_bbox(const float* __restrict__ xyz, int64_t n, float L,
+                                              Meta* m) {
+  float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  bool bad = false;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  int64_t scalar_from = 0;
+  if (VEC) {
+    const int64_t ng = n / 4;
+    const float4* p4 = reinterpret_cast<const float4*>(xyz);
+    for (int64_t g = tid; g < ng; g += nth) {
+      float4 a = __ldg(p4 + 3 * g), b = __ldg(p4 + 3 * g + 1), c = __ldg(p4 + 3 * g + 2);
+      float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int e = 0; e < 12; ++e) {
+        const int d = e % 3;
+        bad |= bad_coord(v[e], L);
+        mn[d] = fminf(mn[d], v[e]);
+        mx[d] = fmaxf(mx[d], v[e]);
+      }
+    }
+    scalar_from = ng * 4;
+  }
+  for (int64_t i = scalar_from + tid; i < n; i += nth) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float v = xyz[3 * i + d];
+      bad |= bad_coord(v, L);
+      mn[d] = fminf(mn[d], v);
+      mx[d] = fmaxf(mx[d], v);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane_id() == 0) set_error(m, JZT_ERR_INPUT, kStageInput);
+  if (L > 0.0f) return;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+      mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+    }
+  }
+  if (lane_id() == 0) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (mn[d] <= mx[d]) {
+        atomicMin(&m->bbox_enc[d], f2sortable(mn[d]));
+        atomicMax(&m->bbox_enc[3 + d], f2sortable(mx[d]));
+      }
+    }
+  }
+}
+
+// Quantisation box: periodic -> origin 0, extent L; open -> origin at the
+// minimum, common extent = the largest side (1 if all points coincide).
+// scale = 2^21 / extent, rounded to nearest in float32.
+__global__ void k_finish_box(Meta* m, float L) {
+  if (threadIdx.x != 0) return;
+  float ext;
+  if (L > 0.0f) {
+    m->lo[0] = m->lo[1] = m->lo[2] = 0.0f;
+    ext = L;
+  } else {
+    ext = 0.0f;
+    for (int d = 0; d < 3; ++d) {
+      float lo = sortable2f(m->bbox_enc[d]);
+      float hi = sortable2f(m->bbox_enc[3 + d]);
+      m->lo[d] = lo;
+      ext = fmaxf(ext, __fsub_rn(hi, lo));
+    }
+    if (!(ext > 0.0f)) ext = 1.0f;
+  }
+  m->scale = __fdiv_rn((float)(1 << kKeyBits), ext);
+}
+
+// ------------------------------------------------------------------ Morton keys
+
+// Spread the low 21 bits of v so that bit j lands at bit 3j.
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffffu;
+  x = (x | (x << 32)) & 0x001f00000000ffffull;
+  x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t quant(float v, float lo, float scale) {
+  float u = __fmul_rn(__fsub_rn(v, lo), scale);
+  uint32_t q = __float2uint_rd(u);
+  return q > (1u << kKeyBits) - 1 ? (1u << kKeyBits) - 1 : q;
+}
+
+// Key bit 3j+2 = q_x bit j, 3j+1 = q_y bit j, 3j = q_z bit j (x most significant).
+__device__ __forceinline__ uint64_t morton(float x, float y, float z, const float* lo, float sc) {
+  return (spread3(quant(x, lo[0], sc)) << 2) | (spread3(quant(y, lo[1], sc)) << 1) |
+         spread3(quant(z, lo[2], sc));
+}
+
+// Histogram of all radix digits of the keys held by a warp (lanes with
+// valid=false contribute nothing); warp-aggregated shared-memory increments.
+__device__ __forceinline__ void hist_key(uint32_t (*sh)[kRadixBins], uint64_t key, bool valid) {
+  const unsigned act = __ballot_sync(0xffffffffu, valid);
+  if (!valid) return;
+#pragma unroll
+  for (int p = 0; p < kRadixPasses; ++p) {
+    uint32_t d = (uint32_t)(key >> (p * kRadixBits)) & (kRadixBins - 1);
+    unsigned peers = __match_any_sync(act, d);
+    if ((int)(__ffs(peers) - 1) == lane_id()) atomicAdd(&sh[p][d], (uint32_t)__popc(peers));
+  }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_keygen(const float* __restrict__ xyz, int64_t n, Meta* m,
+                                                uint64_t* __restrict__ keys) {
+  __shared__ uint32_t sh[kRadixPasses][kRadixBins];
+  for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  const float lo[3] = {m->lo[0], m->lo[1], m->lo[2]};
+  const float sc = m->scale;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int64_t base_tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (VEC) {
+    const int64_t ng = (n + 3) / 4;
+    const int64_t ng_full = n / 4;
+    const float4* p4 = reinterpret_cast<const float4*>(xyz);
+    // iterate so that every lane of a warp runs the same number of rounds
+    const int64_t rounds = (ng + nth - 1) / nth;
+    for (int64_t r = 0; r < rounds; ++r) {
+      int64_t g = r * nth + base_tid;
+      uint64_t k4[4] = {0, 0, 0, 0};
+      int cnt = 0;
+      if (g < ng_full) {
+        float4 a = __ldg(p4 + 3 * g), b = __ldg(p4 + 3 * g + 1), c = __ldg(p4 + 3 * g + 2);
+        k4[0] = morton(a.x, a.y, a.z, lo, sc);
+        k4[1] = morton(a.w, b.x, b.y, lo, sc);
+        k4[2] = morton(b.z, b.w, c.x, lo, sc);
+        k4[3] = morton(c.y, c.z, c.w, lo, sc);
+        ulonglong2* o = reinterpret_cast<ulonglong2*>(keys + 4 * g);
+        o[0] = make_ulonglong2(k4[0], k4[1]);
+        o[1] = make_ulonglong2(k4[2], k4[3]);
+        cnt = 4;
+      } else if (g < ng) {
+        for (int64_t i = 4 * g; i < n; ++i, ++cnt) {
+          k4[cnt] = morton(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lo, sc);
+          keys[i] = k4[cnt];
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) hist_key(sh, k4[e], e < cnt);
+    }
+  } else {
+    const int64_t rounds = (n + nth - 1) / nth;
+    for (int64_t r = 0; r < rounds; ++r) {
+      int64_t i = r * nth + base_tid;
+      uint64_t k = 0;
+      if (i < n) {
+        k = morton(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lo, sc);
+        keys[i] = k;
+      }
+      hist_key(sh, k, i < n);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) {
+    uint32_t v = (&sh[0][0])[i];
+    if (v) atomicAdd(&m->radix_hist[0][0] + i, v);
+  }
+}
+
+// Exclusive digit offsets per pass (one warp per pass).
+__global__ void k_radix_offsets(Meta* m) {
+  const int p = warp_id();
+  if (p >= kRadixPasses) return;
+  uint32_t run = 0;
+  for (int b0 = 0; b0 < kRadixBins; b0 += 32) {
+    uint32_t v = m->radix_hist[p][b0 + lane_id()];
+    uint32_t inc = warp_incl_scan(v);
+    m->radix_offsets[p][b0 + lane_id()] = run + inc - v;
+    run += __shfl_sync(0xffffffffu, inc, 31);
+  }
+}
+
+// ------------------------------------------------------------------ onesweep pass
+//
+// One stable counting pass of the LSD radix sort on digit `pass` (8 bits).
+// Tiles of 4096 keys are claimed in order through an atomic counter, so a tile
+// only ever waits (decoupled look-back) on tiles already running.  Keys are
+// ranked stably per warp with match.any, staged in shared memory in digit
+// order, and written out in runs that are contiguous in global memory.
+struct SortSmem {
+  uint32_t whist[kSortThreads / 32][kRadixBins];
+  uint32_t tile_start[kRadixBins];
+  uint32_t gbase[kRadixBins];
+  uint32_t tile;
+  uint64_t stage_k[kSortTile];
+  uint32_t stage_v[kSortTile];
+};
+
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint64_t* __restrict__ kin,
+                                                           const uint32_t* __restrict__ vin,
+                                                           uint64_t* __restrict__ kout,
+                                                           uint32_t* __restrict__ vout, int64_t n,
+                                                           int pass, uint32_t* lookback, Meta* m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
+  constexpr int W = kSortThreads / 32;
+  const int w = warp_id(), lane = lane_id(), t = threadIdx.x;
+  const int shift = pass * kRadixBits;
+  if (t == 0) S.tile = atomicAdd(&m->tile_ctr[pass], 1u);
+  for (int i = t; i < W * kRadixBins; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t tile = S.tile;
+  const int64_t base = tile * kSortTile;
+  const int tile_n = (int)min64(kSortTile, n - base);
+
+  uint64_t key[kSortIpt];
+  uint32_t val[kSortIpt];
+  uint32_t rank[kSortIpt];
+  const int64_t wbase = base + (int64_t)w * (32 * kSortIpt);
+#pragma unroll
+  for (int i = 0; i < kSortIpt; ++i) {
+    int64_t idx = wbase + i * 32 + lane;
+    bool ok = idx < n;
+    key[i] = ok ? kin[idx] : ~0ull;
+    val[i] = ok ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
+  }
+#pragma unroll
+  for (int i = 0; i < kSortIpt; ++i) {
+    int64_t idx = wbase + i * 32 + lane;
+    uint32_t d = idx < n ? (uint32_t)(key[i] >> shift) & (kRadixBins - 1) : (uint32_t)kRadixBins;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int leader = __ffs(peers) - 1;
+    uint32_t old = 0;
+    if (lane == leader && d < kRadixBins) {
+      old = S.whist[w][d];
+      S.whist[w][d] = old + __popc(peers);
+    }
+    old = __shfl_sync(0xffffffffu, old, leader);
+    rank[i] = old + __popc(peers & lanemask_lt());
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: warp-exclusive prefixes and the tile count
+  uint32_t count;
+  {
+    const int d = t;  // kSortThreads == kRadixBins
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < W; ++ww) {
+      uint32_t v = S.whist[ww][d];
+      S.whist[ww][d] = run;
+      run += v;
+    }
+    count = run;
+  }
+  uint32_t total;
+  uint32_t start = block_excl_scan<kSortThreads>(count, &total);
+  S.tile_start[t] = start;
+  // decoupled look-back, one digit per thread
+  {
+    const int d = t;
+    uint32_t* lb = lookback + (size_t)tile * kRadixBins;
+    if (tile == 0) {
+      st_release_u32(&lb[d], kFlagP | count);
+      S.gbase[d] = m->radix_offsets[pass][d];
+    } else {
+      st_release_u32(&lb[d], kFlagA | count);
+      uint32_t excl = 0;
+      int64_t j = tile - 1;
+      long long spins = 0;
+      while (j >= 0) {
+        uint32_t v = ld_acquire_u32(lookback + (size_t)j * kRadixBins + d);
+        uint32_t f = v & ~kValMask;
+        if (f == 0) {
+          if (++spins > kSpinLimit || failed(m)) {
+            set_error(m, JZT_ERR_TIMEOUT, kStageSort);
+            break;
+          }
+          continue;
+        }
+        excl += v & kValMask;
+        if (f == kFlagP) break;
+        --j;
+      }
+      st_release_u32(&lb[d], kFlagP | (excl + count));
+      S.gbase[d] = m->radix_offsets[pass][d] + excl;
+    }
+  }
+  __syncthreads();
+  // scatter into shared memory in digit order
+#pragma unroll
+  for (int i = 0; i < kSortIpt; ++i) {
+    int64_t idx = wbase + i * 32 + lane;
+    if (idx < n) {
+      uint32_t d = (uint32_t)(key[i] >> shift) & (kRadixBins - 1);
+      uint32_t pos = S.tile_start[d] + S.whist[w][d] + rank[i];
+      S.stage_k[pos] = key[i];
+      S.stage_v[pos] = val[i];
+    }
+  }
+  __syncthreads();
+  for (int j = t; j < tile_n; j += kSortThreads) {
+    uint64_t k = S.stage_k[j];
+    uint32_t d = (uint32_t)(k >> shift) & (kRadixBins - 1);
+    uint32_t g = S.gbase[d] + (uint32_t)j - S.tile_start[d];
+    if (g < (uint64_t)n) {  // always true unless a look-back wait gave up
+      kout[g] = k;
+      vout[g] = S.stage_v[j];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ gather
+__global__ void k_gather(const float* __restrict__ xyz, const uint32_t* __restrict__ perm, int64_t n,
+                         float4* __restrict__ pts) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t p = perm[i];
+    if (p >= (uint64_t)n) p = 0;  // only after a failed sort (status already set)
+    const float* s = xyz + 3 * (int64_t)p;
+    pts[i] = make_float4(__ldg(s), __ldg(s + 1), __ldg(s + 2), __uint_as_float(p));
+  }
+}
+
+// ------------------------------------------------------------------ gap levels
+
+// Level between sorted positions a < b: bit length of the key XOR; for equal
+// keys the positions act as 32 extra low key bits, giving -clz(a ^ b) < 0.
+__device__ __forceinline__ int level_ext(uint64_t ka, uint64_t kb, int64_t a, int64_t b) {
+  uint64_t x = ka ^ kb;
+  return x ? 64 - __clzll((long long)x) : -__clz((int)((uint32_t)a ^ (uint32_t)b));
+}
+
+// Leaf splits of plane 0 (Sec. II-C): gap i (0 < i < N) is a split when the
+// smallest node holding points i-1 and i has n_i > M = N_max^(0) points.  Such a
+// node holds M+1 consecutive points j..j+M around the gap exactly when the
+// level of the pair (j, j+M) does not exceed the gap's level, for some
+// j in [i-M, i-1]; the test reads only the keys within M of the gap (the range
+// search of Sec. II-C, step 2).  Gaps 0 and N are always splits.  The flags
+// are compacted in one pass (chained scan) into spl0 = split gap indices.
+constexpr int kSplitThreads = 256;
+constexpr int kSplitPer = kScanTile / kSplitThreads;  // gaps per thread
+
+__global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const uint64_t* __restrict__ keys,
+                                                               int64_t n, int M, int32_t* spl0,
+                                                               int64_t cap, unsigned long long* st,
+                                                               Meta* m) {
+  __shared__ uint64_t s_key[kScanTile + 2 * 32 + 1];
+  __shared__ int8_t s_w[kScanTile + 32];
+  __shared__ uint32_t s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&m->tile_ctr[kCtrLeafSplits], 1u);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t g0 = tile * kScanTile;
+  // keys at positions [g0 - M, g0 + T + M)
+  const int64_t k0 = g0 - M;
+  const int nk = kScanTile + 2 * M;
+  for (int t = threadIdx.x; t < nk; t += kSplitThreads) {
+    int64_t pos = k0 + t;
+    s_key[t] = (pos >= 0 && pos < n) ? keys[pos] : 0ull;
+  }
+  __syncthreads();
+  // window levels w_j = level(j, j+M) for j in [g0 - M, g0 + T)
+  for (int t = threadIdx.x; t < kScanTile + M; t += kSplitThreads) {
+    int64_t j = k0 + t;
+    int v = 127;
+    if (j >= 0 && j + M < n) v = level_ext(s_key[t], s_key[t + M], j, j + M);
+    s_w[t] = (int8_t)v;
+  }
+  __syncthreads();
+  uint32_t flags = 0;
+  int cnt = 0;
+#pragma unroll
+  for (int r = 0; r < kSplitPer; ++r) {
+    int64_t i = g0 + threadIdx.x * kSplitPer + r;
+    bool f = false;
+    if (i == 0 || i == n) {
+      f = true;
+    } else if (i < n) {
+      int li = (int)(i - k0);  // s_key index of point i
+      int g = level_ext(s_key[li - 1], s_key[li], i - 1, i);
+      int64_t jlo = max64(0, i - M), jhi = min64(i - 1, n - 1 - M);
+      for (int64_t j = jlo; j <= jhi; ++j) {
+        if (s_w[j - k0] <= g) {
+          f = true;
+          break;
+        }
+      }
+    }
+    flags |= (uint32_t)f << r;
+    cnt += f;
+  }
+  uint32_t total;
+  uint32_t local = block_excl_scan<kSplitThreads>((uint32_t)cnt, &total);
+  __shared__ unsigned long long s_base;
+  if (warp_id() == 0) {
+    unsigned long long ex = chained_scan(st, tile, total, m, kStageSplits);
+    if (lane_id() == 0) s_base = ex;
+  }
+  __syncthreads();
+  const unsigned long long base = s_base + local;
+#pragma unroll
+  for (int r = 0, o = 0; r < kSplitPer; ++r) {
+    if (flags >> r & 1u) {
+      int64_t i = g0 + threadIdx.x * kSplitPer + r;
+      unsigned long long pos = base + o++;
+      if (pos <= (unsigned long long)cap) {
+        spl0[pos] = (int32_t)i;
+      } else {
+        set_error(m, JZT_ERR_CAPACITY, kStageSplits);
+      }
+      if (i == n) m->n_nodes[0] = (int32_t)minu64(pos, (unsigned long long)cap);
+    }
+  }
+}
+
+// n_i at every plane-0 split gap (Sec. II-C: binary searches left and right for
+// l_b and r_b; galloping from the gap since most nodes are small).
+__device__ __forceinline__ int64_t first_ge_left(const uint64_t* keys, int64_t hi, int64_t lo_lim,
+                                                 uint64_t target) {
+  // smallest j in [lo_lim, hi] with keys[j] >= target, given keys[hi] >= target
+  int64_t good = hi, step = 1;
+  while (good - step >= lo_lim && keys[good - step] >= target) {
+    good -= step;
+    step <<= 1;
+  }
+  int64_t bad = max64(lo_lim - 1, good - step);  // keys[bad] < target or bad < lo_lim
+  while (good - bad > 1) {
+    int64_t mid = bad + (good - bad) / 2;
+    if (keys[mid] >= target) good = mid; else bad = mid;
+  }
+  return good;
+}
+__device__ __forceinline__ int64_t first_gt_right(const uint64_t* keys, int64_t lo, int64_t hi_lim,
+                                                  uint64_t target) {
+  // smallest j in [lo, hi_lim] with j == hi_lim or keys[j] > target, given keys[lo-1] <= target
+  int64_t good = lo - 1, step = 1;
+  while (good + step < hi_lim && keys[good + step] <= target) {
+    good += step;
+    step <<= 1;
+  }
+  int64_t bad = min64(hi_lim, good + step);
+  while (bad - good > 1) {
+    int64_t mid = good + (bad - good) / 2;
+    if (keys[mid] <= target) good = mid; else bad = mid;
+  }
+  return bad;
+}
+
+__global__ void k_split_sizes(const uint64_t* __restrict__ keys, int64_t n,
+                              const int32_t* __restrict__ spl0, int32_t* __restrict__ nsz,
+                              const Meta* m) {
+  if (failed(m)) return;
+  const int64_t ns = (int64_t)m->n_nodes[0] + 1;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = spl0[s];
+    int64_t sz = n;
+    if (i > 0 && i < n) {
+      uint64_t ka = keys[i - 1], kb = keys[i];
+      int g = level_ext(ka, kb, i - 1, i);
+      if (g > 0) {
+        uint64_t mask = (g >= 64) ? ~0ull : ((1ull << g) - 1ull);
+        uint64_t lo_key = kb & ~mask, hi_key = kb | mask;
+        int64_t lb = first_ge_left(keys, i - 1, 0, lo_key);
+        int64_t rb = first_gt_right(keys, i + 1, n, hi_key);
+        sz = rb - lb;
+      } else {
+        int bits = g + kIndexLevelOffset;
+        int64_t blk = (i >> bits) << bits;
+        int64_t blk_end = min64(n, blk + (1ll << bits));
+        int64_t lb = first_ge_left(keys, i - 1, blk, kb);        // equal keys: keys[j] >= kb
+        int64_t rb = first_gt_right(keys, i + 1, blk_end, kb);   // keys[j] > kb
+        sz = rb - lb;
+      }
+    }
+    nsz[s] = (int32_t)sz;
+  }
+}
+
+// Plane p >= 1: keep the plane p-1 splits whose n exceeds N_max^(p) (plus the
+// two ends); spl[p] holds their positions in plane p-1's split array, gap[p]
+// and nsz[p] carry the point-space gap index and n along.
+__global__ void __launch_bounds__(256) k_coarse_splits(const int32_t* __restrict__ gap_in,
+                                                       const int32_t* __restrict__ nsz_in,
+                                                       int plane_in, int64_t nmax, int32_t* spl,
+                                                       int32_t* gap_out, int32_t* nsz_out,
+                                                       int64_t cap, unsigned long long* st,
+                                                       int ctr, Meta* m) {
+  constexpr int PER = kScanTile / 256;
+  __shared__ uint32_t s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&m->tile_ctr[ctr], 1u);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t nin = (int64_t)m->n_nodes[plane_in] + 1;  // splits of the finer plane
+  const int64_t t0 = tile * kScanTile + threadIdx.x * PER;
+  uint32_t flags = 0;
+  int cnt = 0;
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    int64_t t = t0 + r;
+    bool f = false;
+    if (t < nin) f = (t == 0) || (t == nin - 1) || ((int64_t)nsz_in[t] > nmax);
+    flags |= (uint32_t)f << r;
+    cnt += f;
+  }
+  uint32_t total;
+  uint32_t local = block_excl_scan<256>((uint32_t)cnt, &total);
+  __shared__ unsigned long long s_base;
+  if (warp_id() == 0) {
+    unsigned long long ex = chained_scan(st, tile, total, m, kStageSplits);
+    if (lane_id() == 0) s_base = ex;
+  }
+  __syncthreads();
+  const unsigned long long base = s_base + local;
+#pragma unroll
+  for (int r = 0, o = 0; r < PER; ++r) {
+    if (flags >> r & 1u) {
+      int64_t t = t0 + r;
+      unsigned long long pos = base + o++;
+      if (pos <= (unsigned long long)cap) {
+        spl[pos] = (int32_t)t;
+        gap_out[pos] = gap_in[t];
+        nsz_out[pos] = nsz_in[t];
+      } else {
+        set_error(m, JZT_ERR_CAPACITY, kStageSplits);
+      }
+      if (t == nin - 1) m->n_nodes[plane_in + 1] = (int32_t)minu64(pos, (unsigned long long)cap);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ node records
+// Leaves: one warp per leaf reduces its points' bounding box.
+__global__ void k_leaf_nodes(const float4* __restrict__ pts, const int32_t* __restrict__ spl0,
+                             NodeRec* __restrict__ nodes, const Meta* m) {
+  if (warp_failed(m)) return;
+  const int64_t nn = m->n_nodes[0];
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = lane_id();
+  for (int64_t L = gw; L < nn; L += nw) {
+    int64_t s = spl0[L], e = spl0[L + 1];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = s + lane; i < e; i += 32) {
+      float4 p = pts[i];
+      lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
+      hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+        hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+      }
+    }
+    if (lane == 0) {
+      NodeRec r;
+      r.lo[0] = lo[0]; r.lo[1] = lo[1]; r.lo[2] = lo[2];
+      r.hi[0] = hi[0]; r.hi[1] = hi[1]; r.hi[2] = hi[2];
+      r.count = (int32_t)(e - s);
+      r.first = (int32_t)s;
+      nodes[L] = r;
+    }
+  }
+}
+
+// Plane p >= 1: one warp per node reduces its children's records.
+__global__ void k_upper_nodes(const int32_t* __restrict__ spl, const int32_t* __restrict__ gap,
+                              const NodeRec* __restrict__ child, NodeRec* __restrict__ nodes,
+                              int plane, const Meta* m) {
+  if (warp_failed(m)) return;
+  const int64_t nn = m->n_nodes[plane];
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = lane_id();
+  for (int64_t P = gw; P < nn; P += nw) {
+    int64_t s = spl[P], e = spl[P + 1];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t c = s + lane; c < e; c += 32) {
+      NodeRec r = child[c];
+      lo[0] = fminf(lo[0], r.lo[0]); lo[1] = fminf(lo[1], r.lo[1]); lo[2] = fminf(lo[2], r.lo[2]);
+      hi[0] = fmaxf(hi[0], r.hi[0]); hi[1] = fmaxf(hi[1], r.hi[1]); hi[2] = fmaxf(hi[2], r.hi[2]);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+        hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+      }
+    }
+    if (lane == 0) {
+      NodeRec r;
+      r.lo[0] = lo[0]; r.lo[1] = lo[1]; r.lo[2] = lo[2];
+      r.hi[0] = hi[0]; r.hi[1] = hi[1]; r.hi[2] = hi[2];
+      r.count = gap[P + 1] - gap[P];
+      r.first = (int32_t)s;
+      nodes[P] = r;
+    }
+  }
+}
+
+// Super nodes (Alg. 1): NGR consecutive top nodes per super node.
+__global__ void k_super_splits(int32_t* spl_super, int top_plane, int ngr, int64_t cap, Meta* m) {
+  const int64_t ntop = m->n_nodes[top_plane];
+  const int64_t nsup = (ntop + ngr - 1) / ngr;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (nsup > cap) set_error(m, JZT_ERR_CAPACITY, kStageTop);
+    m->n_nodes[top_plane + 1] = (int32_t)min64(nsup, cap);
+  }
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s <= min64(nsup, cap);
+       s += (int64_t)gridDim.x * blockDim.x)
+    spl_super[s] = (int32_t)min64(s * ngr, ntop);
+}
+
+int grid_for(int64_t work, int threads, int max_blocks) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+}  // namespace
+
+void launch_super_level(const Layout& L, char* ws, cudaStream_t s) {
+  Meta* m = at<Meta>(ws, L.meta);
+  const int P = L.n_planes;
+  k_super_splits<<<grid_for(L.cap_nodes[P] + 1, 256, 1024), 256, 0, s>>>(
+      at<int32_t>(ws, L.spl[P]), P - 1, L.ngr, L.cap_nodes[P], m);
+}
+
+void launch_build(const float* d_xyz, int64_t n, float periodic_L, const Layout& L, char* ws,
+                  cudaStream_t s) {
+  Meta* m = at<Meta>(ws, L.meta);
+  const int sms = 152;
+  k_init_meta<<<1, 256, 0, s>>>(m, L.n_planes);
+  const bool vec = (reinterpret_cast<uintptr_t>(d_xyz) & 15u) == 0;
+  const int gb = grid_for((n + 3) / 4, 256, sms * 8);
+  if (vec) k_bbox<true><<<gb, 256, 0, s>>>(d_xyz, n, periodic_L, m);
+  else k_bbox<false><<<gb, 256, 0, s>>>(d_xyz, n, periodic_L, m);
+  k_finish_box<<<1, 32, 0, s>>>(m, periodic_L);
+  uint64_t* keys_a = at<uint64_t>(ws, L.keys_a);
+  uint64_t* keys_b = at<uint64_t>(ws, L.keys_b);
+  uint32_t* vals_a = at<uint32_t>(ws, L.vals_a);
+  uint32_t* vals_b = at<uint32_t>(ws, L.vals_b);
+  if (vec) k_keygen<true><<<gb, 256, 0, s>>>(d_xyz, n, m, keys_a);
+  else k_keygen<false><<<gb, 256, 0, s>>>(d_xyz, n, m, keys_a);
+  k_radix_offsets<<<1, 32 * kRadixPasses, 0, s>>>(m);
+  // look-back tables of all passes, zeroed once
+  uint32_t* lookback = at<uint32_t>(ws, L.lookback);
+  const int64_t lb_words = L.n_tiles_sort * kRadixBins * kRadixPasses;
+  k_zero_u64<<<grid_for(lb_words / 2 + 1, 256, sms * 8), 256, 0, s>>>(
+      reinterpret_cast<unsigned long long*>(lookback), (lb_words + 1) / 2);
+  const size_t smem = sizeof(SortSmem);
+  cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const uint64_t* kin = keys_a;
+  const uint32_t* vin = nullptr;
+  uint64_t* kout = keys_b;
+  uint32_t* vout = vals_b;
+  for (int p = 0; p < kRadixPasses; ++p) {
+    k_onesweep<<<(unsigned)L.n_tiles_sort, kSortThreads, smem, s>>>(
+        kin, vin, kout, vout, n, p, lookback + (size_t)p * L.n_tiles_sort * kRadixBins, m);
+    kin = kout;
+    vin = vout;
+    kout = (kout == keys_b) ? keys_a : keys_b;
+    vout = (vout == vals_b) ? vals_a : vals_b;
+  }
+  // kRadixPasses is even: the sorted keys and permutation end in keys_a / vals_a
+  static_assert(kRadixPasses % 2 == 0, "sorted output must land in buffer a");
+  float4* pts = at<float4>(ws, L.pts);
+  k_gather<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(d_xyz, vals_a, n, pts);
+
+  // plane 0: leaf splits, then n_i at every leaf split
+  unsigned long long* st = at<unsigned long long>(ws, L.scan_flags);
+  const int64_t split_tiles = (n + 1 + kScanTile - 1) / kScanTile;
+  k_zero_u64<<<grid_for(split_tiles, 256, sms * 8), 256, 0, s>>>(st, split_tiles);
+  k_leaf_splits<<<(unsigned)split_tiles, kSplitThreads, 0, s>>>(
+      keys_a, n, L.nmax0, at<int32_t>(ws, L.spl[0]), L.cap_nodes[0], st, m);
+  k_split_sizes<<<grid_for(L.cap_nodes[0] + 1, 256, sms * 16), 256, 0, s>>>(
+      keys_a, n, at<int32_t>(ws, L.spl[0]), at<int32_t>(ws, L.nsz[0]), m);
+  // coarser planes
+  int64_t nmax = L.nmax0;
+  for (int p = 1; p < L.n_planes; ++p) {
+    nmax *= L.c;
+    const int64_t tiles = (L.cap_nodes[p - 1] + 1 + kScanTile - 1) / kScanTile;
+    k_zero_u64<<<grid_for(tiles, 256, sms * 8), 256, 0, s>>>(st, tiles);
+    k_coarse_splits<<<(unsigned)tiles, 256, 0, s>>>(
+        at<int32_t>(ws, L.gap[p - 1]), at<int32_t>(ws, L.nsz[p - 1]), p - 1, nmax,
+        at<int32_t>(ws, L.spl[p]), at<int32_t>(ws, L.gap[p]), at<int32_t>(ws, L.nsz[p]),
+        L.cap_nodes[p], st, kCtrCoarse + p, m);
+  }
+  // node records
+  k_leaf_nodes<<<grid_for((L.cap_nodes[0]) * 32, 256, sms * 16), 256, 0, s>>>(
+      pts, at<int32_t>(ws, L.spl[0]), at<NodeRec>(ws, L.nodes[0]), m);
+  for (int p = 1; p < L.n_planes; ++p)
+    k_upper_nodes<<<grid_for(L.cap_nodes[p] * 32, 256, sms * 16), 256, 0, s>>>(
+        at<int32_t>(ws, L.spl[p]), at<int32_t>(ws, L.gap[p]), at<NodeRec>(ws, L.nodes[p - 1]),
+        at<NodeRec>(ws, L.nodes[p]), p, m);
+}
+
+}  // namespace jzt

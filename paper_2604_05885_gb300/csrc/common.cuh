@@ -1,0 +1,268 @@
+// Internal definitions shared by the translation units of libjzt.so:
+// the device status/meta block, the workspace layout, and small device helpers
+// (sortable float encoding, directed-rounding box distances, bounded waits).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/jzt.h"
+
+namespace jzt {
+
+constexpr int kMaxPlanes = 14;          // planes 0..kMaxPlanes-1, plus the super level
+constexpr int kKeyBits = 21;            // per coordinate; 63-bit keys (Sec. II-A)
+constexpr int kSentinelLevel = 64;      // level of the gaps before the first / after the last point
+constexpr int kIndexLevelOffset = 32;   // equal keys: level = bit_length((i-1)^i) - 32
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kRadixPasses = (3 * kKeyBits + kRadixBits - 1) / kRadixBits;  // 8
+constexpr int kSortThreads = 256;
+constexpr int kSortIpt = 16;
+constexpr int kSortTile = kSortThreads * kSortIpt;  // 4096 keys per tile
+constexpr int kScanTile = 1024;                      // elements per compaction tile
+constexpr int kMaxK = 32;
+constexpr int kCtrLeafSplits = 8;
+constexpr int kCtrCoarse = 9;   // + plane
+constexpr int kCtrWalk = 24;
+constexpr long long kSpinLimit = 1ll << 22;          // bounded waits (iterations)
+constexpr int kCasLimit = 1 << 20;                   // bounded union-find retries
+
+// Stage identifiers stored in Meta::detail on failure.
+enum Stage : int32_t {
+  kStageNone = 0,
+  kStageInput = 1,
+  kStageSort = 2,
+  kStageSplits = 3,
+  kStageNodes = 4,
+  kStageTop = 5,
+  kStageWalk = 6,
+  kStageLeaf = 7,
+  kStageFof = 8,
+};
+
+// Device-resident status and bookkeeping; lives at offset 0 of the workspace.
+struct Meta {
+  int32_t status;            // jzt_error of the first failure (0 = ok)
+  int32_t detail;            // Stage of the first failure
+  int64_t required_bytes;    // capacity failures: workspace bytes at least needed
+  uint32_t bbox_enc[6];      // sortable-encoded min x,y,z then max x,y,z (open boxes)
+  float lo[3];               // quantisation origin
+  float scale;               // 2^21 / extent (float32)
+  int32_t n_nodes[kMaxPlanes + 1];   // nodes per plane; [n_planes] = super nodes
+  uint32_t tile_ctr[32];     // dynamic tile counters: [0,8) radix passes, 8 leaf splits,
+                             // 9+p coarse plane p, 24.. walk kernels
+  unsigned long long arena_used;     // interaction-list entries handed out
+  unsigned long long arena_peak;     // largest arena_used seen this walk
+  int32_t n_planes;
+  int32_t pad;
+  unsigned long long pair_off[kMaxPlanes + 1];  // FoF: pair list of each plane in the arena
+  unsigned long long pair_cnt[kMaxPlanes + 1];
+  uint32_t radix_offsets[kRadixPasses][kRadixBins];  // exclusive digit offsets per pass
+  uint32_t radix_hist[kRadixPasses][kRadixBins];     // digit histograms per pass
+};
+
+// Workspace layout: byte offsets of every sub-buffer (host-computed).
+struct Layout {
+  int64_t n;
+  int32_t nmax0, c, n_target, ngr, heap;
+  int32_t n_planes;
+  int64_t cap_nodes[kMaxPlanes + 1];  // [n_planes] = super-node capacity
+  int64_t cap_ilist;                  // entries
+  int64_t n_tiles_sort;
+  size_t meta, keys_a, keys_b, vals_a, vals_b, lookback, pts, scan_flags;
+  size_t spl[kMaxPlanes + 1];   // int32 split arrays (cap_nodes+1); [n_planes] = super splits
+  size_t gap[kMaxPlanes];       // int32 point-space gap index of each split
+  size_t nsz[kMaxPlanes];       // int32 n_i at every split of each plane
+  size_t nodes[kMaxPlanes];     // NodeRec per node
+  size_t ilo[kMaxPlanes + 1];   // uint2 (offset, count) per receiving node; [n_planes] = supers
+  size_t arena;                 // IEntry[cap_ilist]
+  size_t ig[kMaxPlanes];        // FoF: int32 group pointer per node
+  size_t lk[kMaxPlanes];        // FoF: uint8 linked flag per node
+  size_t ig_pt;                 // FoF: int32 group pointer per sorted point
+  size_t minorig;               // FoF: int32 smallest original index per root
+  size_t total;
+};
+
+// 32-byte node record: bounding box, point count, first element.
+struct __align__(16) NodeRec {
+  float lo[3];
+  int32_t count;   // points in the node
+  float hi[3];
+  int32_t first;   // first point (plane 0) or first child (plane >= 1)
+};
+
+// Interaction-list entry (Sec. III-A): source node and the squared lower
+// node-node distance r_low^2 (rounded down) used for sorting and early exit.
+struct __align__(8) IEntry {
+  int32_t src;
+  float r2low;
+};
+
+struct Params {
+  int32_t nmax0, c, n_target, ngr, heap;
+  float fac_nodes, fac_ilist;
+};
+
+// ---------------------------------------------------------------- host API
+int resolve_params(const jzt_params* p, Params* out, const char** why);
+int num_planes(int64_t n, const Params& P);
+int compute_layout(int64_t n, const Params& P, Layout* L);
+
+// ---------------------------------------------------------------- launchers
+// build_tree.cu
+void launch_build(const float* d_xyz, int64_t n, float periodic_L, const Layout& L,
+                  char* ws, cudaStream_t s);
+// walk_knn.cu
+void launch_knn(const Layout& L, char* ws, float periodic_L, int k, int order, int32_t* d_idx,
+                float* d_d2, cudaStream_t s);
+// walk_fof.cu
+void launch_fof(const Layout& L, char* ws, float periodic_L, float b, int32_t* d_labels,
+                cudaStream_t s);
+// shared (build_tree.cu)
+void launch_super_level(const Layout& L, char* ws, cudaStream_t s);
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+__host__ __device__ __forceinline__ unsigned long long minu64(unsigned long long a, unsigned long long b) {
+  return a < b ? a : b;
+}
+
+template <typename T>
+__host__ __device__ inline T* at(char* ws, size_t off) { return reinterpret_cast<T*>(ws + off); }
+
+// ---------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+
+__device__ __forceinline__ void set_error(Meta* m, int32_t code, int32_t stage) {
+  if (atomicCAS(&m->status, 0, code) == 0) m->detail = stage;
+}
+
+__device__ __forceinline__ bool failed(const Meta* m) {
+  return *reinterpret_cast<const volatile int32_t*>(&m->status) != 0;
+}
+
+// Same test, uniform across the warp (lane 0 decides), for kernels that use
+// warp collectives after the check.
+__device__ __forceinline__ bool warp_failed(const Meta* m) {
+  int f = 0;
+  if ((threadIdx.x & 31) == 0) f = failed(m) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, f, 0) != 0;
+}
+
+// Order-preserving map float -> uint32 (total order on non-NaN floats).
+__device__ __forceinline__ uint32_t f2sortable(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float sortable2f(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ int warp_id() { return threadIdx.x >> 5; }
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Relative slack applied to box-distance bounds so that they stay conservative
+// with respect to float32 point distances (each of which carries < 2^-21 error).
+constexpr float kLowSlack = 1.0f - 1.0f / 1048576.0f;   // 1 - 2^-20
+constexpr float kHighSlack = 1.0f + 1.0f / 1048576.0f;  // 1 + 2^-20
+
+// Per-dimension lower / upper separation of two closed intervals, rounded down /
+// up.  Periodic (L > 0): minimum over the images -L, 0, +L for the gap; for the
+// span, min over images of the farthest pair, capped at L/2 (minimum image).
+__device__ __forceinline__ float gap_rd(float alo, float ahi, float blo, float bhi) {
+  return fmaxf(0.0f, fmaxf(__fsub_rd(blo, ahi), __fsub_rd(alo, bhi)));
+}
+__device__ __forceinline__ float span_ru(float alo, float ahi, float blo, float bhi) {
+  return fmaxf(__fsub_ru(bhi, alo), __fsub_ru(ahi, blo));
+}
+__device__ __forceinline__ float gap_rd_per(float alo, float ahi, float blo, float bhi, float L) {
+  float g0 = gap_rd(alo, ahi, blo, bhi);
+  float g1 = gap_rd(alo, ahi, __fadd_rd(blo, L), __fadd_ru(bhi, L));
+  float g2 = gap_rd(alo, ahi, __fsub_rd(blo, L), __fsub_ru(bhi, L));
+  return fminf(g0, fminf(g1, g2));
+}
+__device__ __forceinline__ float span_ru_per(float alo, float ahi, float blo, float bhi, float L) {
+  float s0 = span_ru(alo, ahi, blo, bhi);
+  float s1 = span_ru(alo, ahi, __fadd_rd(blo, L), __fadd_ru(bhi, L));
+  float s2 = span_ru(alo, ahi, __fsub_rd(blo, L), __fsub_ru(bhi, L));
+  return fminf(fminf(s0, fminf(s1, s2)), __fmul_ru(0.5f, L));
+}
+
+// Squared lower / upper box-box distances (d_low, d_up of Sec. III-B), as
+// conservative float32 bounds.
+template <bool PERIODIC>
+__device__ __forceinline__ float box_dlow2(const float* alo, const float* ahi, const float* blo,
+                                           const float* bhi, float L) {
+  float s = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float g = PERIODIC ? gap_rd_per(alo[d], ahi[d], blo[d], bhi[d], L)
+                       : gap_rd(alo[d], ahi[d], blo[d], bhi[d]);
+    s = __fmaf_rd(g, g, s);
+  }
+  return s * kLowSlack;
+}
+template <bool PERIODIC>
+__device__ __forceinline__ float box_dup2(const float* alo, const float* ahi, const float* blo,
+                                          const float* bhi, float L) {
+  float s = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float g = PERIODIC ? span_ru_per(alo[d], ahi[d], blo[d], bhi[d], L)
+                       : span_ru(alo[d], ahi[d], blo[d], bhi[d]);
+    s = __fmaf_ru(g, g, s);
+  }
+  return __fmul_ru(s, kHighSlack);
+}
+
+// Union-find on int32 parent pointers that always point to a smaller index
+// (so each root is its set's minimum).  Path halving with plain stores is safe:
+// a pointer is only ever replaced by one of its own ancestors.
+__device__ __forceinline__ int uf_find(int32_t* p, int x) {
+  volatile int32_t* vp = p;
+  // pointers strictly decrease along a path, so the walk ends; the bound only
+  // guards against corrupted input
+  for (int it = 0; it < (1 << 26); ++it) {
+    int px = vp[x];
+    if (px == x) return x;
+    int ppx = vp[px];
+    if (ppx == px) return px;
+    vp[x] = ppx;  // halve the path: ppx is an ancestor of x
+    x = ppx;
+  }
+  return x;
+}
+
+// Link the sets of a and b (higher root -> lower root) with CAS; returns false if
+// the bounded retry budget ran out.
+__device__ __forceinline__ bool uf_union(int32_t* p, int a, int b) {
+  for (int it = 0; it < kCasLimit; ++it) {
+    int ra = uf_find(p, a), rb = uf_find(p, b);
+    if (ra == rb) return true;
+    int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
+    if (atomicCAS(p + hi, hi, lo) == hi) return true;
+  }
+  return false;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace jzt

@@ -1,0 +1,71 @@
+"""Tree construction parity (Sec. II) against the oracle, bit-exact: Morton keys,
+stable sort order, gathered points, plane splits, node counts and boxes."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests.gpu_util import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    x_dup = workloads.uniform(3000, 4)
+    x_dup[100:400] = x_dup[100]          # a run of 300 identical points
+    x_dup[1000:1040] = x_dup[7]
+    x_line = np.zeros((700, 3), np.float32)
+    x_line[:, 0] = workloads.uniform(700, 5)[:, 0]
+    return [
+        ("uniform-open", workloads.uniform(5000, 1), 0.0, None),
+        ("uniform-periodic", workloads.uniform(4099, 2), 1.0, None),
+        ("clustered-periodic-3planes", workloads.clustered(20000, 3, n_blobs=30), 1.0,
+         dict(n_target=10)),
+        ("duplicates", x_dup, 0.0, dict(nmax0=8, plane_factor=4, n_target=4)),
+        ("line", x_line, 0.0, dict(nmax0=4, plane_factor=2, n_target=8)),
+        ("lattice", workloads.lattice(9), 1.0, dict(nmax0=16)),
+        ("tiny-1", workloads.uniform(1, 6), 0.0, None),
+        ("tiny-2", workloads.uniform(2, 6), 1.0, None),
+        ("tiny-33", workloads.uniform(33, 6), 0.0, None),
+        ("ragged-tiles", workloads.uniform(4096 * 3 + 17, 8), 0.0, dict(nmax0=5, n_target=30)),
+    ]
+
+
+@pytest.mark.parametrize("name,x,L,params", _cases(), ids=[c[0] for c in _cases()])
+def test_tree_matches_oracle(name, x, L, params):
+    import paper_2604_05885_gb300 as jzt
+    p = dict(params or {})
+    nmax0 = p.get("nmax0", 32)
+    c = p.get("plane_factor", 8)
+    nt = p.get("n_target", 1000)
+    tree = jzt.build(to_dev(x), periodic_L=L, params=p or None)
+    st = tree.status()
+    assert st["code"] == 0, st
+    keys, pts, n_planes = tree.arrays()
+    assert n_planes == oracle.num_planes(len(x), nmax0, c, nt)
+    ref_keys = oracle.morton_keys(x, L)
+    sk, perm = oracle.zsort(ref_keys)
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), sk)
+    p_np = pts.cpu().numpy()
+    assert np.array_equal(p_np[:, 3].view(np.int32), perm.astype(np.int32))
+    assert np.array_equal(p_np[:, :3], x[perm])
+    spl_ref, gaps_ref = oracle.plane_splits(sk, nmax0=nmax0, c=c, n_target=nt)
+    nodes_ref = oracle.plane_nodes(x[perm], gaps_ref)
+    for pl in range(n_planes):
+        spl, cnt, box = tree.plane(pl)
+        assert np.array_equal(spl, spl_ref[pl].astype(np.int32)), f"plane {pl} splits"
+        rc, rlo, rhi = nodes_ref[pl]
+        assert np.array_equal(cnt, rc.astype(np.int32)), f"plane {pl} counts"
+        assert np.array_equal(box[:, :3], rlo) and np.array_equal(box[:, 3:], rhi), f"plane {pl} boxes"
+
+
+def test_invalid_coordinates_set_input_status():
+    import paper_2604_05885_gb300 as jzt
+    x = workloads.uniform(1000, 9)
+    x[17, 1] = np.nan
+    tree = jzt.build(to_dev(x), periodic_L=0.0)
+    assert tree.status()["code"] == jzt.JZT_ERR_INPUT
+    x = workloads.uniform(1000, 9)
+    x[3, 0] = 1.0  # outside [0, L) for L = 1
+    tree = jzt.build(to_dev(x), periodic_L=1.0)
+    assert tree.status()["code"] == jzt.JZT_ERR_INPUT
