@@ -76,8 +76,11 @@ typedef struct jzt_status_info {
 } jzt_status_info;
 
 /* Workspace size for N points and parameters p (NULL = defaults).  k_or_0 is the
- * largest k the caller will ask for (0 if only FoF); it does not change the size
- * in this version but is validated (1..32).  Host-only, no CUDA call.
+ * largest k the caller will ask for (0 if only FoF): the interaction-list part
+ * grows with k above 16.  The interaction-list arena is the last part of the
+ * workspace and takes all of it that remains, so a caller that gets
+ * JZT_ERR_CAPACITY can retry with a larger workspace (see
+ * jzt_status_info.required_bytes) and the same parameters.  Host-only.
  * Errors: JZT_ERR_INVALID for N out of range, bad parameters or null `bytes`. */
 int jzt_workspace_bytes(int64_t n, int k_or_0, const jzt_params *p, size_t *bytes);
 

@@ -152,13 +152,14 @@ class Tree:
     """A tree built in a caller-owned workspace (see jzt_build)."""
 
     def __init__(self, xyz: torch.Tensor, periodic_L: float = 0.0, params=None,
-                 workspace: torch.Tensor | None = None, stream=None):
+                 workspace: torch.Tensor | None = None, stream=None, k_max: int = 32):
         _check_xyz(xyz)
         n = xyz.shape[0]
         self.n = n
         self.periodic_L = float(periodic_L)
         self.params = params
-        self.workspace = workspace if workspace is not None else alloc_workspace(n, 0, params, xyz.device)
+        self.workspace = workspace if workspace is not None else alloc_workspace(
+            n, min(int(k_max), n, 32), params, xyz.device)
         self._h = ctypes.c_void_p(0)
         _check(lib.jzt_build(ctypes.c_void_p(xyz.data_ptr()), n, self.periodic_L, _params(params),
                              ctypes.c_void_p(self.workspace.data_ptr()), self.workspace.numel(),
@@ -217,15 +218,15 @@ class Tree:
             self._h = ctypes.c_void_p(0)
 
 
-def build(xyz, periodic_L=0.0, params=None, workspace=None, stream=None) -> Tree:
-    return Tree(xyz, periodic_L, params, workspace, stream)
+def build(xyz, periodic_L=0.0, params=None, workspace=None, stream=None, k_max=32) -> Tree:
+    return Tree(xyz, periodic_L, params, workspace, stream, k_max)
 
 
 def knn(xyz: torch.Tensor, k: int, periodic_L: float = 0.0, workspace=None, stream=None, check=True):
     """One-call exact kNN (jzt_knn); returns (idx [N,k] int32, dist2 [N,k] float32)."""
     _check_xyz(xyz)
     n = xyz.shape[0]
-    ws = workspace if workspace is not None else alloc_workspace(n, k, None, xyz.device)
+    ws = workspace if workspace is not None else alloc_workspace(n, min(k, n), None, xyz.device)
     idx = torch.empty((n, k), dtype=torch.int32, device=xyz.device)
     d2 = torch.empty((n, k), dtype=torch.float32, device=xyz.device)
     _check(lib.jzt_knn(ctypes.c_void_p(xyz.data_ptr()), n, int(k), float(periodic_L),

@@ -73,7 +73,7 @@ int num_planes(int64_t n, const Params& P) {
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-int compute_layout(int64_t n, const Params& P, Layout* Lp) {
+int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* Lp) {
   Layout L;
   std::memset(&L, 0, sizeof(L));
   L.n = n;
@@ -83,9 +83,13 @@ int compute_layout(int64_t n, const Params& P, Layout* Lp) {
   L.ngr = P.ngr;
   L.heap = P.heap;
   L.n_planes = num_planes(n, P);
+  // Node capacity per plane: fac * N / (N_max^(p)/2) (Eq. alloc_nodes).  The
+  // estimate is not a bound (Sec. II-C), so the small upper planes get 4x the
+  // estimate plus slack; never more than the plane below.
   double nmax = P.nmax0;
   for (int p = 0; p < L.n_planes; ++p) {
     double est = std::ceil((double)P.fac_nodes * (double)n / (nmax / 2.0));
+    if (p > 0) est = 4.0 * est + 256.0;
     int64_t cap = (int64_t)std::min<double>(est, (double)n);
     if (p > 0) cap = std::min<int64_t>(cap, L.cap_nodes[p - 1]);
     L.cap_nodes[p] = std::max<int64_t>(cap, 1);
@@ -93,8 +97,6 @@ int compute_layout(int64_t n, const Params& P, Layout* Lp) {
   }
   const int64_t cap_sup = (L.cap_nodes[L.n_planes - 1] + P.ngr - 1) / P.ngr;
   L.cap_nodes[L.n_planes] = cap_sup;
-  L.cap_ilist = (int64_t)std::ceil((double)P.fac_ilist * (double)n / ((double)P.nmax0 / 2.0)) +
-                cap_sup * cap_sup + 1024;
   L.n_tiles_sort = (n + kSortTile - 1) / kSortTile;
 
   size_t off = 0;
@@ -118,12 +120,25 @@ int compute_layout(int64_t n, const Params& P, Layout* Lp) {
   for (int p = 0; p < L.n_planes; ++p) L.nsz[p] = take(4 * (size_t)(L.cap_nodes[p] + 1));
   for (int p = 0; p < L.n_planes; ++p) L.nodes[p] = take(sizeof(NodeRec) * (size_t)L.cap_nodes[p]);
   for (int p = 0; p <= L.n_planes; ++p) L.ilo[p] = take(8 * (size_t)L.cap_nodes[p]);
-  L.arena = take(sizeof(IEntry) * (size_t)L.cap_ilist);
   for (int p = 0; p < L.n_planes; ++p) L.ig[p] = take(4 * (size_t)L.cap_nodes[p]);
   for (int p = 0; p < L.n_planes; ++p) L.lk[p] = take((size_t)L.cap_nodes[p]);
   L.ig_pt = take(4 * (size_t)n);
   L.minorig = take(4 * (size_t)n);
-  L.total = off;
+  // Interaction-list arena (Eq. alloc_ilist): fac * N / (N_max^(0)/2) entries,
+  // scaled by k/16 for k > 16, plus the dense super-node list; last in the
+  // workspace so that a larger workspace simply grows it.
+  L.arena = off;
+  const int64_t min_entries = cap_sup * cap_sup + 1024;
+  if (ws_bytes == 0) {
+    const double kfac = std::max(1.0, (double)k / 16.0);
+    L.cap_ilist = (int64_t)std::ceil((double)P.fac_ilist * kfac * (double)n / ((double)P.nmax0 / 2.0)) +
+                  min_entries;
+  } else {
+    L.cap_ilist = ws_bytes > off ? (int64_t)((ws_bytes - off) / sizeof(IEntry)) : 0;
+  }
+  L.cap_ilist = std::min<int64_t>(L.cap_ilist, (int64_t)0xffffffffll);  // 32-bit list offsets
+  if (ws_bytes != 0 && L.cap_ilist < min_entries) L.cap_ilist = -1;     // too small
+  L.total = align256(L.arena + sizeof(IEntry) * (size_t)std::max<int64_t>(L.cap_ilist, min_entries));
   *Lp = L;
   return JZT_OK;
 }
@@ -164,7 +179,7 @@ int jzt_workspace_bytes(int64_t n, int k_or_0, const jzt_params* p, size_t* byte
   const char* why = nullptr;
   if (int e = resolve_params(p, &P, &why)) return fail(e, why);
   Layout L;
-  compute_layout(n, P, &L);
+  compute_layout(n, P, k_or_0, 0, &L);
   *bytes = L.total;
   return JZT_OK;
 }
@@ -182,10 +197,13 @@ int jzt_build(const float* d_xyz, int64_t n, float periodic_L, const jzt_params*
   const char* why = nullptr;
   if (int e = resolve_params(p, &P, &why)) return fail(e, why);
   Layout L;
-  compute_layout(n, P, &L);
-  if (ws_bytes < L.total)
-    return fail(JZT_ERR_WORKSPACE, "workspace too small: need " + std::to_string(L.total) +
+  compute_layout(n, P, 0, ws_bytes, &L);
+  if (L.cap_ilist < 0) {
+    Layout need;
+    compute_layout(n, P, 0, 0, &need);
+    return fail(JZT_ERR_WORKSPACE, "workspace too small: need " + std::to_string(need.total) +
                                        " bytes, got " + std::to_string(ws_bytes));
+  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   launch_build(d_xyz, n, periodic_L > 0.0f ? periodic_L : 0.0f, L, static_cast<char*>(d_ws), s);
   cudaError_t e = cudaGetLastError();

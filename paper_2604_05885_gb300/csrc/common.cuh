@@ -107,7 +107,9 @@ struct Params {
 // ---------------------------------------------------------------- host API
 int resolve_params(const jzt_params* p, Params* out, const char** why);
 int num_planes(int64_t n, const Params& P);
-int compute_layout(int64_t n, const Params& P, Layout* L);
+// ws_bytes == 0: size the interaction-list arena for k (jzt_workspace_bytes);
+// otherwise the arena takes the whole remainder of a ws_bytes workspace.
+int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* L);
 
 // ---------------------------------------------------------------- launchers
 // build_tree.cu
@@ -247,6 +249,18 @@ __device__ __forceinline__ int uf_find(int32_t* p, int x) {
     if (ppx == px) return px;
     vp[x] = ppx;  // halve the path: ppx is an ancestor of x
     x = ppx;
+  }
+  return x;
+}
+
+// Root of x without writing anything: used where other threads store final
+// (contracted) pointers concurrently, which a path-halving store could undo.
+__device__ __forceinline__ int uf_root_ro(const int32_t* p, int x) {
+  const volatile int32_t* vp = p;
+  for (int it = 0; it < (1 << 26); ++it) {
+    int px = vp[x];
+    if (px == x) return x;
+    x = px;
   }
   return x;
 }

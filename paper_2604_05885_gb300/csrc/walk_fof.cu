@@ -176,7 +176,7 @@ __global__ void k_contract(int32_t* ig, int plane, int64_t n_fixed, const Meta* 
   const int64_t nn = plane >= 0 ? (int64_t)m->n_nodes[plane] : n_fixed;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn;
        i += (int64_t)gridDim.x * blockDim.x)
-    ig[i] = uf_find(ig, (int)i);
+    ig[i] = uf_root_ro(ig, (int)i);
 }
 
 // Plane p -> p-1 (Eq. igroup): one warp per parent.

@@ -11,8 +11,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _lib():
-    from paper_2604_05885_gb300 import _build
-    _build.build()
+    import __graft_entry__
+    __graft_entry__._builder().build()
     import paper_2604_05885_gb300 as jzt
     return jzt
 

@@ -82,3 +82,21 @@ def test_permutation_invariance():
     perm = np.random.default_rng(2).permutation(len(x))
     c = jzt.build(to_dev(x[perm]), periodic_L=1.0).fof(b).cpu().numpy()
     assert np.array_equal(oracle.canonical_labels(a[perm]), c)
+
+
+def test_repeated_runs_near_percolation():
+    """Many concurrent unions (b near the percolation threshold): every repeat of
+    the walk must give the oracle's labels, so no union or contraction is lost
+    to a race."""
+    import paper_2604_05885_gb300 as jzt
+    n = 20000
+    x = workloads.uniform(n, 21)
+    b = 0.9 * workloads.mean_spacing(n)
+    s, lo = oracle.fof_bracket(x, b, 0.0, cells=True)
+    for nt in (10, 1000):
+        tree = jzt.build(to_dev(x), periodic_L=0.0, params=dict(n_target=nt))
+        for _ in range(6):
+            lab = tree.fof(b).cpu().numpy()
+            assert tree.status()["code"] == 0
+            from tests import parity
+            parity.check_fof(lab, s, lo)
