@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Throughput benchmark: exact kNN (k = 16) and FoF (b = 0.2 mean spacing) on
+2^27 = 512^3 points (Zel'dovich-displaced lattice in a periodic unit box).
+
+One step = build the tree (keys, radix sort, planes, nodes) + kNN walk + FoF
+walk on device-resident points; value = particles per second for the whole job
+(all ranks).  Multi-GPU runs are independent replicas (the workload does not
+shard), so scaling is weak.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the only other implementation of this
+path here) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "kNN(k=16) & FoF(b=0.2) particles/s at N=2^27 on 1 GB300; p50/p99 served latency"
+UNIT = "particles/s"
+FLOPS_PER_PAIR = 8        # dx, dy, dz, dx*dx, 2 fma (fma = 2 flops)
+FP32_LANES_PER_SM = 128
+SMS = 152
+SORT_BYTES_PER_PT = 24    # one LSD pass: read key+value, write key+value (8+4 each way)
+BUILD_FLOOR_BYTES = 42    # read xyz 12 + sorted float4 16 + keys/perm 12 + tree ~2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-side", type=int, default=512)
+    ap.add_argument("--k", type=int, default=16)
+    ap.add_argument("--b-frac", type=float, default=0.2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-side", type=float, default=0.25,
+                    help="side of the sub-cube timed per step by --impl reference")
+    ap.add_argument("--cpu-side", type=float, default=0.375,
+                    help="side of the sub-cube of the workload timed on the CPU")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cache", default=os.path.join(tempfile.gettempdir(), "jzt_bench_cache"))
+    return ap.parse_args()
+
+
+def workload(n_side, cache):
+    import numpy as np
+    import workloads
+    os.makedirs(cache, exist_ok=True)
+    path = os.path.join(cache, f"zeldovich_{n_side}_seed3.npy")
+    if os.path.exists(path):
+        return np.load(path)
+    x = workloads.zeldovich(n_side, 3)
+    np.save(path + ".tmp.npy", x)
+    os.replace(path + ".tmp.npy", path)
+    return x
+
+
+class Clocks:
+    """nvidia-smi sampler over the timed region (SM clocks and throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [v.strip() for v in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return float("nan")
+        sm = sorted(num(r[1]) for r in rows)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(num(r[2]) for r in rows),
+                "power_w_max": max(num(r[3]) for r in rows), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+def cpu_baseline(x, n_side, k, b, side, threads=0):
+    """The oracle (cell-list kNN + cell-list FoF, all host cores) on the points of
+    the sub-cube [0, side)^3 of the workload, treated as an open box."""
+    import numpy as np
+    import oracle
+    sel = np.all(x < np.float32(side), axis=1)
+    xs = np.ascontiguousarray(x[sel])
+    cores = oracle.num_threads(threads)
+    t0 = time.perf_counter()
+    oracle.knn_cells(xs, k, 0.0, threads=threads)
+    t1 = time.perf_counter()
+    oracle.fof_cells(xs, b, 0.0, threads=threads)
+    t2 = time.perf_counter()
+    n = xs.shape[0]
+    return {"value": n / (t2 - t0), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} points of the sub-cube [0,{side})^3 of the {n_side}^3 Zel'dovich set, "
+                      f"open box; cell-list kNN k={k} ({t1 - t0:.1f} s) + cell-list FoF ({t2 - t1:.1f} s)",
+            "seconds": t2 - t0}
+
+
+def dist_setup(gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+        pg = dist
+    return rank, world, local, pg
+
+
+def main():
+    a = parse()
+    rank, world, local, dist = dist_setup(a.gpus)
+    n_side = a.n_side
+    n = n_side ** 3
+    k = a.k
+    b = a.b_frac / n_side
+    L = 1.0
+    cfg = {"workload": f"zeldovich-{n_side}^3-periodic", "n": n, "k": k, "b": b, "periodic_L": L,
+           "step": "build + kNN(k) + FoF(b) on device-resident points",
+           "parallelism": f"replicas x{world}", "l2": "inputs (12 B/pt) larger than L2 (129 MB)"}
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        x = workload(n_side, a.cache)
+        import numpy as np  # noqa: F401
+        vals = []
+        for s in range(a.warmup + a.steps):
+            cb = cpu_baseline(x, n_side, k, b, a.ref_side)
+            if s >= a.warmup:
+                vals.append(cb)
+        v = sorted(c["value"] for c in vals)[len(vals) // 2]
+        cb = dict(vals[-1])
+        cb["value"] = v
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": 1000.0 * sum(c["seconds"] for c in vals) / len(vals),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": cfg, "cpu_baseline": cb,
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2604_05885_gb300 as jzt
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    x = workload(n_side, a.cache)
+    x_dev = torch.from_numpy(x).to(dev)
+    ws = jzt.alloc_workspace(n, k, None, dev)
+    idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+    d2 = torch.empty((n, k), dtype=torch.float32, device=dev)
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(xd):
+        tree = jzt.build(xd, periodic_L=L, workspace=ws)
+        tree.knn(k, out=(idx, d2))
+        tree.fof(b, out=lab)
+        return tree
+
+    for _ in range(a.warmup):
+        tree = step(x_dev)
+    st = tree.status(raise_on_error=True)
+    jzt.profile_read()  # discard warm-up records
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = Clocks(local)
+    barrier()
+    jzt.profile_enable(True)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        tree = step(x_dev)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    jzt.profile_enable(False)
+    ms_total = e0.elapsed_time(e1)
+    phase_ms, phase_cnt, launches = jzt.profile_read()
+    st = tree.status(raise_on_error=True)
+    ms_step = ms_total / a.steps
+    if dist is not None:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * n / (ms_step / 1000.0)
+
+    # end to end through host buffers (pinned): input H2D, outputs D2H, every step
+    e2e = None
+    if a.e2e_steps > 0:
+        try:
+            x_host = torch.from_numpy(x).pin_memory()
+            idx_h = torch.empty((n, k), dtype=torch.int32).pin_memory()
+            d2_h = torch.empty((n, k), dtype=torch.float32).pin_memory()
+            lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
+            x_in = torch.empty_like(x_dev)
+            barrier()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(a.e2e_steps):
+                x_in.copy_(x_host, non_blocking=True)
+                step(x_in)
+                idx_h.copy_(idx, non_blocking=True)
+                d2_h.copy_(d2, non_blocking=True)
+                lab_h.copy_(lab, non_blocking=True)
+            f1.record(stream)
+            barrier()
+            ms_e2e = f0.elapsed_time(f1) / a.e2e_steps
+            if dist is not None:
+                t = torch.tensor([ms_e2e], device=dev)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                ms_e2e = float(t.item())
+            h2d = x_host.numel() * 4
+            d2h = idx_h.numel() * 4 + d2_h.numel() * 4 + lab_h.numel() * 4
+            e2e = {"value": world * n / (ms_e2e / 1000.0), "unit": UNIT, "ms_per_step": ms_e2e,
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            jzt.profile_read()
+        except RuntimeError as exc:  # pinned allocation refused
+            e2e = {"value": None, "unit": UNIT, "error": str(exc)[:200]}
+
+    # rooflines ----------------------------------------------------------------
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as fh:
+            peaks = json.load(fh)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    alu_peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    steps = a.steps
+    per = {ph: (phase_ms[ph] / phase_cnt[ph] if phase_cnt[ph] else 0.0) for ph in phase_ms}
+    l2l_ms = per.get("knn_l2l", 0.0)
+    pairs_per_launch = st["knn_pairs"]
+    achieved = pairs_per_launch * FLOPS_PER_PAIR / (l2l_ms / 1000.0) / 1e12 if l2l_ms else 0.0
+    roofline = {"kernel": "k_l2l_knn", "bound": "alu", "achieved": achieved, "peak": alu_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak_tflops if alu_peak_tflops else None,
+                "traffic": None, "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock sampled)",
+                "work": f"{pairs_per_launch} point pairs x {FLOPS_PER_PAIR} flops per launch",
+                "ms_per_launch": l2l_ms}
+    sort_ms = phase_ms.get("sort", 0.0) / max(1, phase_cnt.get("sort", 0))
+    sort_launch_ms = sort_ms / 8.0
+    sort_gbs = SORT_BYTES_PER_PT * n / (sort_launch_ms / 1000.0) / 1e9 if sort_ms else 0.0
+    build_ms = sum(per.get(ph, 0.0) for ph in ("box", "keys", "sort", "gather", "splits", "nodes"))
+    build_floor_gbs = BUILD_FLOOR_BYTES * n / (build_ms / 1000.0) / 1e9 if build_ms else 0.0
+    roof_sort = {"kernel": "k_onesweep", "bound": "hbm", "achieved": sort_gbs, "peak": hbm_peak,
+                 "unit": "GB/s", "frac": sort_gbs / hbm_peak, "traffic": None,
+                 "peak_source": hbm_src, "work": f"{SORT_BYTES_PER_PT} B/pt x {n} per pass",
+                 "ms_per_launch": sort_launch_ms}
+    roof_build = {"stage": "build (box, keys, sort, gather, splits, nodes)", "bound": "hbm",
+                  "achieved": build_floor_gbs, "peak": hbm_peak, "unit": "GB/s",
+                  "frac": build_floor_gbs / hbm_peak, "work": f"{BUILD_FLOOR_BYTES} B/pt algorithmic floor",
+                  "ms": build_ms}
+    knn_ms = sum(per.get(ph, 0.0) * phase_cnt.get(ph, 0) / steps for ph in ("knn_top", "knn_n2n", "knn_sort", "knn_l2l"))
+    fof_ms = sum(per.get(ph, 0.0) * phase_cnt.get(ph, 0) / steps for ph in ("fof_top", "fof_n2n", "fof_l2l", "fof_labels"))
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "roofline_sort": roof_sort, "roofline_build": roof_build,
+            "phases_ms_per_step": {ph: phase_ms[ph] / steps for ph in phase_ms},
+            "knn_particles_per_s": n / ((build_ms + knn_ms) / 1000.0) if knn_ms else None,
+            "fof_particles_per_s": n / ((build_ms + fof_ms) / 1000.0) if fof_ms else None,
+            "knn_pairs_per_point": st["knn_pairs"] / n, "fof_pairs_per_point": st["fof_pairs"] / n,
+            "ilist_entries": st["ilist_entries"], "n_nodes": [v for v in st["n_nodes"] if v],
+            "p50_p99_latency": None}
+    if rank == 0 and not a.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(x, n_side, k, b, a.cpu_side)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

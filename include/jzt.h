@@ -72,7 +72,9 @@ typedef struct jzt_status_info {
     int64_t ilist_entries;    /* interaction-list entries used by the last walk */
     int32_t n_planes;         /* tree-planes built (Sec. II-C) */
     int32_t reserved;
-    int64_t n_nodes[16];      /* nodes per plane, plane 0 = leaves */
+    int64_t n_nodes[16];      /* nodes per plane, plane 0 = leaves; [n_planes] = super nodes */
+    int64_t knn_pairs;        /* point pairs evaluated by the last kNN LeafToLeaf */
+    int64_t fof_pairs;        /* point pairs evaluated by the last FoF LeafToLeaf */
 } jzt_status_info;
 
 /* Workspace size for N points and parameters p (NULL = defaults).  k_or_0 is the
@@ -143,6 +145,20 @@ int jzt_tree_plane(const jzt_tree *t, int p, int64_t cap, int64_t *n_nodes,
                    int32_t *spl, int32_t *count, float *box, void *stream);
 
 void jzt_tree_free(jzt_tree *t);
+
+/* Instrumentation (no counterpart in the paper; used to measure the kernels).
+ * jzt_profile_enable(1) makes every later call record a CUDA event pair on its
+ * own stream around each kernel phase (phase names: jzt_profile_phase_name).
+ * jzt_profile_read waits for the recorded events, writes the summed duration
+ * in milliseconds and the number of recorded instances of phase i to ms[i] and
+ * counts[i] (i < n; either array may be NULL), writes to *launches the number of
+ * kernels this library launched since the previous read (counted whether or
+ * not profiling is on; may be NULL), and clears the records.  Host-only state,
+ * shared by all threads; returns JZT_ERR_CUDA if an event could not be read. */
+int jzt_profile_enable(int on);
+int jzt_profile_read(double *ms, int64_t *counts, int n, int64_t *launches);
+/* Name of phase i, or NULL past the last phase. */
+const char *jzt_profile_phase_name(int i);
 
 /* Thread-local description of the last error returned on this thread. */
 const char *jzt_last_error(void);

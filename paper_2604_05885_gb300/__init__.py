@@ -39,7 +39,7 @@ _NAMES = {0: "ok", -1: "invalid", -2: "unsupported", -3: "cuda", -4: "workspace"
 # Every entry point declared in include/jzt.h.
 SYMBOLS = ("jzt_workspace_bytes", "jzt_build", "jzt_tree_knn", "jzt_tree_fof", "jzt_knn", "jzt_fof",
            "jzt_status", "jzt_tree_arrays", "jzt_tree_plane", "jzt_tree_free", "jzt_last_error",
-           "jzt_version")
+           "jzt_version", "jzt_profile_enable", "jzt_profile_read", "jzt_profile_phase_name")
 
 
 class JztError(RuntimeError):
@@ -60,7 +60,8 @@ class StatusInfo(ctypes.Structure):
     _fields_ = [("code", ctypes.c_int32), ("detail", ctypes.c_int32),
                 ("required_bytes", ctypes.c_int64), ("ilist_entries", ctypes.c_int64),
                 ("n_planes", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("n_nodes", ctypes.c_int64 * 16)]
+                ("n_nodes", ctypes.c_int64 * 16), ("knn_pairs", ctypes.c_int64),
+                ("fof_pairs", ctypes.c_int64)]
 
 
 def _load():
@@ -78,6 +79,13 @@ def _load():
     lib.jzt_status.argtypes = [vp, vp, ctypes.POINTER(StatusInfo)]
     lib.jzt_tree_arrays.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32)]
     lib.jzt_tree_plane.argtypes = [vp, ctypes.c_int, i64, ctypes.POINTER(i64), vp, vp, vp, vp]
+    lib.jzt_profile_enable.argtypes = [ctypes.c_int]
+    lib.jzt_profile_enable.restype = ctypes.c_int
+    lib.jzt_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), ctypes.c_int,
+                                     ctypes.POINTER(i64)]
+    lib.jzt_profile_read.restype = ctypes.c_int
+    lib.jzt_profile_phase_name.argtypes = [ctypes.c_int]
+    lib.jzt_profile_phase_name.restype = ctypes.c_char_p
     lib.jzt_tree_free.argtypes = [vp]
     lib.jzt_tree_free.restype = None
     lib.jzt_last_error.restype = ctypes.c_char_p
@@ -142,10 +150,35 @@ def status(workspace: torch.Tensor, stream=None, raise_on_error: bool = False) -
         _check(rc)
     out = dict(code=info.code, name=_NAMES.get(info.code, str(info.code)), detail=info.detail,
                required_bytes=info.required_bytes, ilist_entries=info.ilist_entries,
-               n_planes=info.n_planes, n_nodes=[info.n_nodes[i] for i in range(16)])
+               n_planes=info.n_planes, n_nodes=[info.n_nodes[i] for i in range(16)],
+               knn_pairs=info.knn_pairs, fof_pairs=info.fof_pairs)
     if raise_on_error and info.code != JZT_OK:
         raise JztError(info.code, lib.jzt_last_error().decode())
     return out
+
+
+def phase_names() -> list[str]:
+    out = []
+    while True:
+        nm = lib.jzt_profile_phase_name(len(out))
+        if nm is None:
+            return out
+        out.append(nm.decode())
+
+
+def profile_enable(on: bool = True):
+    lib.jzt_profile_enable(1 if on else 0)
+
+
+def profile_read() -> tuple[dict, dict, int]:
+    """(ms per phase, instances per phase, kernel launches) since the last read."""
+    names = phase_names()
+    n = len(names)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    launches = ctypes.c_int64(0)
+    _check(lib.jzt_profile_read(ms, cnt, n, ctypes.byref(launches)))
+    return ({names[i]: ms[i] for i in range(n)}, {names[i]: cnt[i] for i in range(n)}, int(launches.value))
 
 
 class Tree:

@@ -286,6 +286,8 @@ int jzt_status(const void* d_ws, void* stream, jzt_status_info* info) {
     info->ilist_entries = (int64_t)m.arena_peak;
     info->n_planes = m.n_planes;
     for (int p = 0; p < 16 && p < kMaxPlanes + 1; ++p) info->n_nodes[p] = m.n_nodes[p];
+    info->knn_pairs = (int64_t)m.knn_pairs;
+    info->fof_pairs = (int64_t)m.fof_pairs;
   }
   if (m.status != 0) {
     static const char* names[] = {"ok", "invalid", "unsupported", "cuda", "workspace",
@@ -347,5 +349,16 @@ int jzt_tree_plane(const jzt_tree* t, int p, int64_t cap, int64_t* n_nodes, int3
 }
 
 void jzt_tree_free(jzt_tree* t) { delete t; }
+
+int jzt_profile_enable(int on) { return profile_enable(on); }
+
+int jzt_profile_read(double* ms, int64_t* counts, int n, int64_t* launches) {
+  long long l = 0;
+  int rc = profile_read(ms, counts, n, &l);
+  if (launches) *launches = (int64_t)l;
+  return rc ? fail(JZT_ERR_CUDA, "jzt_profile_read: event query failed") : JZT_OK;
+}
+
+const char* jzt_profile_phase_name(int i) { return phase_name(i); }
 
 }  // extern "C"

@@ -773,31 +773,38 @@ void launch_super_level(const Layout& L, char* ws, cudaStream_t s) {
   Meta* m = at<Meta>(ws, L.meta);
   const int P = L.n_planes;
   k_super_splits<<<grid_for(L.cap_nodes[P] + 1, 256, 1024), 256, 0, s>>>(
-      at<int32_t>(ws, L.spl[P]), P - 1, L.ngr, L.cap_nodes[P], m);
+      at<int32_t>(ws, L.spl[P]), P - 1, L.ngr, L.cap_nodes[P], m); note_launch();
 }
 
 void launch_build(const float* d_xyz, int64_t n, float periodic_L, const Layout& L, char* ws,
                   cudaStream_t s) {
   Meta* m = at<Meta>(ws, L.meta);
   const int sms = 152;
-  k_init_meta<<<1, 256, 0, s>>>(m, L.n_planes);
+  prof_begin(kPhBox, s);
+  k_init_meta<<<1, 256, 0, s>>>(m, L.n_planes); note_launch();
   const bool vec = (reinterpret_cast<uintptr_t>(d_xyz) & 15u) == 0;
   const int gb = grid_for((n + 3) / 4, 256, sms * 8);
   if (vec) k_bbox<true><<<gb, 256, 0, s>>>(d_xyz, n, periodic_L, m);
   else k_bbox<false><<<gb, 256, 0, s>>>(d_xyz, n, periodic_L, m);
-  k_finish_box<<<1, 32, 0, s>>>(m, periodic_L);
+  note_launch();
+  k_finish_box<<<1, 32, 0, s>>>(m, periodic_L); note_launch();
+  prof_end(kPhBox, s);
+  prof_begin(kPhKeys, s);
   uint64_t* keys_a = at<uint64_t>(ws, L.keys_a);
   uint64_t* keys_b = at<uint64_t>(ws, L.keys_b);
   uint32_t* vals_a = at<uint32_t>(ws, L.vals_a);
   uint32_t* vals_b = at<uint32_t>(ws, L.vals_b);
   if (vec) k_keygen<true><<<gb, 256, 0, s>>>(d_xyz, n, m, keys_a);
   else k_keygen<false><<<gb, 256, 0, s>>>(d_xyz, n, m, keys_a);
-  k_radix_offsets<<<1, 32 * kRadixPasses, 0, s>>>(m);
+  note_launch();
+  k_radix_offsets<<<1, 32 * kRadixPasses, 0, s>>>(m); note_launch();
   // look-back tables of all passes, zeroed once
   uint32_t* lookback = at<uint32_t>(ws, L.lookback);
   const int64_t lb_words = L.n_tiles_sort * kRadixBins * kRadixPasses;
   k_zero_u64<<<grid_for(lb_words / 2 + 1, 256, sms * 8), 256, 0, s>>>(
-      reinterpret_cast<unsigned long long*>(lookback), (lb_words + 1) / 2);
+      reinterpret_cast<unsigned long long*>(lookback), (lb_words + 1) / 2); note_launch();
+  prof_end(kPhKeys, s);
+  prof_begin(kPhSort, s);
   const size_t smem = sizeof(SortSmem);
   cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const uint64_t* kin = keys_a;
@@ -806,7 +813,7 @@ void launch_build(const float* d_xyz, int64_t n, float periodic_L, const Layout&
   uint32_t* vout = vals_b;
   for (int p = 0; p < kRadixPasses; ++p) {
     k_onesweep<<<(unsigned)L.n_tiles_sort, kSortThreads, smem, s>>>(
-        kin, vin, kout, vout, n, p, lookback + (size_t)p * L.n_tiles_sort * kRadixBins, m);
+        kin, vin, kout, vout, n, p, lookback + (size_t)p * L.n_tiles_sort * kRadixBins, m); note_launch();
     kin = kout;
     vin = vout;
     kout = (kout == keys_b) ? keys_a : keys_b;
@@ -814,35 +821,42 @@ void launch_build(const float* d_xyz, int64_t n, float periodic_L, const Layout&
   }
   // kRadixPasses is even: the sorted keys and permutation end in keys_a / vals_a
   static_assert(kRadixPasses % 2 == 0, "sorted output must land in buffer a");
+  prof_end(kPhSort, s);
+  prof_begin(kPhGather, s);
   float4* pts = at<float4>(ws, L.pts);
-  k_gather<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(d_xyz, vals_a, n, pts);
+  k_gather<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(d_xyz, vals_a, n, pts); note_launch();
 
+  prof_end(kPhGather, s);
+  prof_begin(kPhSplits, s);
   // plane 0: leaf splits, then n_i at every leaf split
   unsigned long long* st = at<unsigned long long>(ws, L.scan_flags);
   const int64_t split_tiles = (n + 1 + kScanTile - 1) / kScanTile;
-  k_zero_u64<<<grid_for(split_tiles, 256, sms * 8), 256, 0, s>>>(st, split_tiles);
+  k_zero_u64<<<grid_for(split_tiles, 256, sms * 8), 256, 0, s>>>(st, split_tiles); note_launch();
   k_leaf_splits<<<(unsigned)split_tiles, kSplitThreads, 0, s>>>(
-      keys_a, n, L.nmax0, at<int32_t>(ws, L.spl[0]), L.cap_nodes[0], st, m);
+      keys_a, n, L.nmax0, at<int32_t>(ws, L.spl[0]), L.cap_nodes[0], st, m); note_launch();
   k_split_sizes<<<grid_for(L.cap_nodes[0] + 1, 256, sms * 16), 256, 0, s>>>(
-      keys_a, n, at<int32_t>(ws, L.spl[0]), at<int32_t>(ws, L.nsz[0]), m);
+      keys_a, n, at<int32_t>(ws, L.spl[0]), at<int32_t>(ws, L.nsz[0]), m); note_launch();
   // coarser planes
   int64_t nmax = L.nmax0;
   for (int p = 1; p < L.n_planes; ++p) {
     nmax *= L.c;
     const int64_t tiles = (L.cap_nodes[p - 1] + 1 + kScanTile - 1) / kScanTile;
-    k_zero_u64<<<grid_for(tiles, 256, sms * 8), 256, 0, s>>>(st, tiles);
+    k_zero_u64<<<grid_for(tiles, 256, sms * 8), 256, 0, s>>>(st, tiles); note_launch();
     k_coarse_splits<<<(unsigned)tiles, 256, 0, s>>>(
         at<int32_t>(ws, L.gap[p - 1]), at<int32_t>(ws, L.nsz[p - 1]), p - 1, nmax,
         at<int32_t>(ws, L.spl[p]), at<int32_t>(ws, L.gap[p]), at<int32_t>(ws, L.nsz[p]),
-        L.cap_nodes[p], st, kCtrCoarse + p, m);
+        L.cap_nodes[p], st, kCtrCoarse + p, m); note_launch();
   }
+  prof_end(kPhSplits, s);
+  prof_begin(kPhNodes, s);
   // node records
   k_leaf_nodes<<<grid_for((L.cap_nodes[0]) * 32, 256, sms * 16), 256, 0, s>>>(
-      pts, at<int32_t>(ws, L.spl[0]), at<NodeRec>(ws, L.nodes[0]), m);
+      pts, at<int32_t>(ws, L.spl[0]), at<NodeRec>(ws, L.nodes[0]), m); note_launch();
   for (int p = 1; p < L.n_planes; ++p)
     k_upper_nodes<<<grid_for(L.cap_nodes[p] * 32, 256, sms * 16), 256, 0, s>>>(
         at<int32_t>(ws, L.spl[p]), at<int32_t>(ws, L.gap[p]), at<NodeRec>(ws, L.nodes[p - 1]),
-        at<NodeRec>(ws, L.nodes[p]), p, m);
+        at<NodeRec>(ws, L.nodes[p]), p, m); note_launch();
+  prof_end(kPhNodes, s);
 }
 
 }  // namespace jzt

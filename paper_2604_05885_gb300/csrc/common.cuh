@@ -56,6 +56,8 @@ struct Meta {
   unsigned long long arena_peak;     // largest arena_used seen this walk
   int32_t n_planes;
   int32_t pad;
+  unsigned long long knn_pairs;      // point pairs evaluated by the kNN LeafToLeaf
+  unsigned long long fof_pairs;      // point pairs evaluated by the FoF LeafToLeaf
   unsigned long long pair_off[kMaxPlanes + 1];  // FoF: pair list of each plane in the arena
   unsigned long long pair_cnt[kMaxPlanes + 1];
   uint32_t radix_offsets[kRadixPasses][kRadixBins];  // exclusive digit offsets per pass
@@ -110,6 +112,19 @@ int num_planes(int64_t n, const Params& P);
 // ws_bytes == 0: size the interaction-list arena for k (jzt_workspace_bytes);
 // otherwise the arena takes the whole remainder of a ws_bytes workspace.
 int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* L);
+
+// ---------------------------------------------------------------- instrumentation (prof.cu)
+enum Phase : int {
+  kPhBox = 0, kPhKeys, kPhSort, kPhGather, kPhSplits, kPhNodes,
+  kPhKnnTop, kPhKnnN2N, kPhKnnSort, kPhKnnL2L,
+  kPhFofTop, kPhFofN2N, kPhFofL2L, kPhFofLabels, kPhaseCount
+};
+void note_launch(int n = 1);
+void prof_begin(int phase, cudaStream_t s);
+void prof_end(int phase, cudaStream_t s);
+const char* phase_name(int i);
+int profile_enable(int on);
+int profile_read(double* ms, int64_t* counts, int n, long long* launches);
 
 // ---------------------------------------------------------------- launchers
 // build_tree.cu

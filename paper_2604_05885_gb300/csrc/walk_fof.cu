@@ -35,6 +35,7 @@ __global__ void k_fof_reset(Meta* m) {
   if (threadIdx.x == 0) {
     m->arena_used = 0;
     m->arena_peak = 0;
+    m->fof_pairs = 0;
   }
   if (threadIdx.x < kMaxPlanes + 1) {
     m->pair_off[threadIdx.x] = 0;
@@ -239,10 +240,13 @@ __global__ void __launch_bounds__(128) k_l2l_fof(const float4* __restrict__ pts,
   const float invL = PER ? 1.0f / L : 0.0f;
   const float halfL = 0.5f * L;
   bool union_fail = false;
+  unsigned long long pairs = 0;
   for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < np; t += nw) {
     const int2 pr = arena[off + t];
     const NodeRec A = leaves[pr.x], B = leaves[pr.y];
     const bool self = pr.x == pr.y;
+    pairs += self ? (unsigned long long)A.count * (A.count - 1) / 2
+                  : (unsigned long long)A.count * B.count;
     float sh[3] = {0.f, 0.f, 0.f};
     bool ambiguous = false;
     if (PER) {
@@ -285,6 +289,7 @@ __global__ void __launch_bounds__(128) k_l2l_fof(const float4* __restrict__ pts,
     }
   }
   if (union_fail) set_error(m, JZT_ERR_TIMEOUT, kStageFof);
+  if (lane == 0 && pairs) atomicAdd(&m->fof_pairs, pairs);
 }
 
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
@@ -326,37 +331,45 @@ void fof_all(const Layout& L, char* ws, float pl, float b, int32_t* labels, cuda
   const float b2 = b * b;  // float32, round to nearest
   int2* arena = at<int2>(ws, L.arena);
   const int64_t cap = L.cap_ilist;  // IEntry and int2 are both 8 bytes
-  k_fof_reset<<<1, 32, 0, s>>>(m);
+  prof_begin(kPhFofTop, s);
+  k_fof_reset<<<1, 32, 0, s>>>(m); note_launch();
   launch_super_level(L, ws, s);
   k_fof_super_pairs<<<grid_for(L.cap_nodes[P], 128, sms * 4), 128, 0, s>>>(arena, P, cap,
-                                                                            (int64_t)L.total, m);
+                                                                            (int64_t)L.total, m); note_launch();
   k_fof_init_top<<<grid_for(L.cap_nodes[P - 1], 256, sms * 8), 256, 0, s>>>(
       at<NodeRec>(ws, L.nodes[P - 1]), at<int32_t>(ws, L.ig[P - 1]), at<uint8_t>(ws, L.lk[P - 1]),
-      P - 1, pl, b2, m);
+      P - 1, pl, b2, m); note_launch();
+  prof_end(kPhFofTop, s);
   for (int p = P - 1; p >= 0; --p) {
-    k_mark_plane_start<<<1, 32, 0, s>>>(m, p);
+    prof_begin(kPhFofN2N, s);
+    k_mark_plane_start<<<1, 32, 0, s>>>(m, p); note_launch();
     k_n2n_fof<PER><<<grid_for(L.cap_nodes[p + 1] * 32, 32 * kFofWarps, sms * 16), 32 * kFofWarps, 0, s>>>(
         at<int32_t>(ws, L.spl[p + 1]), at<NodeRec>(ws, L.nodes[p]), at<int32_t>(ws, L.ig[p]),
-        at<uint8_t>(ws, L.lk[p]), arena, p + 1, pl, b2, cap, (int64_t)L.total, m);
-    k_mark_plane_end<<<1, 32, 0, s>>>(m, p);
-    k_contract<<<grid_for(L.cap_nodes[p], 256, sms * 8), 256, 0, s>>>(at<int32_t>(ws, L.ig[p]), p, 0, m);
+        at<uint8_t>(ws, L.lk[p]), arena, p + 1, pl, b2, cap, (int64_t)L.total, m); note_launch();
+    k_mark_plane_end<<<1, 32, 0, s>>>(m, p); note_launch();
+    k_contract<<<grid_for(L.cap_nodes[p], 256, sms * 8), 256, 0, s>>>(at<int32_t>(ws, L.ig[p]), p, 0, m); note_launch();
     if (p > 0) {
       k_parent_to_node<PER><<<grid_for(L.cap_nodes[p] * 32, 256, sms * 16), 256, 0, s>>>(
           at<int32_t>(ws, L.spl[p]), at<int32_t>(ws, L.ig[p]), at<uint8_t>(ws, L.lk[p]),
           at<NodeRec>(ws, L.nodes[p - 1]), at<int32_t>(ws, L.ig[p - 1]), at<uint8_t>(ws, L.lk[p - 1]),
-          p, pl, b2, m);
+          p, pl, b2, m); note_launch();
     }
+    prof_end(kPhFofN2N, s);
   }
   int32_t* ig_pt = at<int32_t>(ws, L.ig_pt);
+  prof_begin(kPhFofL2L, s);
   k_leaf_to_points<<<grid_for(L.cap_nodes[0] * 32, 256, sms * 16), 256, 0, s>>>(
-      at<int32_t>(ws, L.spl[0]), at<int32_t>(ws, L.ig[0]), at<uint8_t>(ws, L.lk[0]), ig_pt, m);
+      at<int32_t>(ws, L.spl[0]), at<int32_t>(ws, L.ig[0]), at<uint8_t>(ws, L.lk[0]), ig_pt, m); note_launch();
   k_l2l_fof<PER><<<sms * 16, 128, 0, s>>>(at<float4>(ws, L.pts), at<NodeRec>(ws, L.nodes[0]), arena,
-                                          ig_pt, pl, b2, m);
-  k_contract<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(ig_pt, -1, n, m);
+                                          ig_pt, pl, b2, m); note_launch();
+  prof_end(kPhFofL2L, s);
+  prof_begin(kPhFofLabels, s);
+  k_contract<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(ig_pt, -1, n, m); note_launch();
   int32_t* minorig = at<int32_t>(ws, L.minorig);
-  k_fill_i32<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(minorig, n, INT_MAX);
-  k_group_min<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(at<float4>(ws, L.pts), ig_pt, minorig, n);
-  k_labels<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(at<float4>(ws, L.pts), ig_pt, minorig, labels, n, m);
+  k_fill_i32<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(minorig, n, INT_MAX); note_launch();
+  k_group_min<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(at<float4>(ws, L.pts), ig_pt, minorig, n); note_launch();
+  k_labels<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(at<float4>(ws, L.pts), ig_pt, minorig, labels, n, m); note_launch();
+  prof_end(kPhFofLabels, s);
 }
 
 }  // namespace
