@@ -324,6 +324,9 @@ def main():
             "fof_particles_per_s": n / ((build_ms + fof_ms) / 1000.0) if fof_ms else None,
             "knn_pairs_per_point": st["knn_pairs"] / n, "fof_pairs_per_point": st["fof_pairs"] / n,
             "ilist_entries": st["ilist_entries"], "n_nodes": [v for v in st["n_nodes"] if v],
+            "knn_plane_entries": [v for v in st["knn_plane_entries"] if v],
+            "knn_l2l_entries_examined": st["knn_stats"][0], "knn_l2l_leaves_scanned": st["knn_stats"][1],
+            "knn_l2l_candidates_queued": st["knn_stats"][2], "knn_l2l_heap_insertions": st["knn_stats"][3],
             "p50_p99_latency": None}
     if rank == 0 and not a.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(x, n_side, k, b, a.cpu_side)

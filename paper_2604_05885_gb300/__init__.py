@@ -61,7 +61,8 @@ class StatusInfo(ctypes.Structure):
                 ("required_bytes", ctypes.c_int64), ("ilist_entries", ctypes.c_int64),
                 ("n_planes", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("n_nodes", ctypes.c_int64 * 16), ("knn_pairs", ctypes.c_int64),
-                ("fof_pairs", ctypes.c_int64)]
+                ("fof_pairs", ctypes.c_int64), ("knn_stats", ctypes.c_int64 * 8),
+                ("knn_plane_entries", ctypes.c_int64 * 16)]
 
 
 def _load():
@@ -151,7 +152,9 @@ def status(workspace: torch.Tensor, stream=None, raise_on_error: bool = False) -
     out = dict(code=info.code, name=_NAMES.get(info.code, str(info.code)), detail=info.detail,
                required_bytes=info.required_bytes, ilist_entries=info.ilist_entries,
                n_planes=info.n_planes, n_nodes=[info.n_nodes[i] for i in range(16)],
-               knn_pairs=info.knn_pairs, fof_pairs=info.fof_pairs)
+               knn_pairs=info.knn_pairs, fof_pairs=info.fof_pairs,
+               knn_stats=[info.knn_stats[i] for i in range(8)],
+               knn_plane_entries=[info.knn_plane_entries[i] for i in range(16)])
     if raise_on_error and info.code != JZT_OK:
         raise JztError(info.code, lib.jzt_last_error().decode())
     return out

@@ -287,6 +287,8 @@ int jzt_status(const void* d_ws, void* stream, jzt_status_info* info) {
     info->n_planes = m.n_planes;
     for (int p = 0; p < 16 && p < kMaxPlanes + 1; ++p) info->n_nodes[p] = m.n_nodes[p];
     info->knn_pairs = (int64_t)m.knn_pairs;
+    for (int t = 0; t < 8; ++t) info->knn_stats[t] = (int64_t)m.knn_stats[t];
+    for (int p = 0; p < 16 && p < kMaxPlanes; ++p) info->knn_plane_entries[p] = (int64_t)m.knn_plane_entries[p];
     info->fof_pairs = (int64_t)m.fof_pairs;
   }
   if (m.status != 0) {

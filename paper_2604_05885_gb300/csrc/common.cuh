@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/jzt.h"
+#include "jzt.h"
 
 namespace jzt {
 
@@ -57,6 +57,8 @@ struct Meta {
   int32_t n_planes;
   int32_t pad;
   unsigned long long knn_pairs;      // point pairs evaluated by the kNN LeafToLeaf
+  unsigned long long knn_stats[8];   // kNN walk statistics (see jzt_status_info)
+  unsigned long long knn_plane_entries[kMaxPlanes];  // interaction-list entries per plane
   unsigned long long fof_pairs;      // point pairs evaluated by the FoF LeafToLeaf
   unsigned long long pair_off[kMaxPlanes + 1];  // FoF: pair list of each plane in the arena
   unsigned long long pair_cnt[kMaxPlanes + 1];

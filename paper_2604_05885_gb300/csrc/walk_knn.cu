@@ -44,6 +44,8 @@ __global__ void k_walk_reset(Meta* m) {
     m->arena_peak = 0;
     m->knn_pairs = 0;
   }
+  if (threadIdx.x < 8) m->knn_stats[threadIdx.x] = 0;
+  if (threadIdx.x < kMaxPlanes) m->knn_plane_entries[threadIdx.x] = 0;
   if (threadIdx.x >= kCtrWalk && threadIdx.x < 32) m->tile_ctr[threadIdx.x] = 0;
 }
 
@@ -140,22 +142,183 @@ struct RHeap {
 };
 
 // ------------------------------------------------------------------ NodeToNode (kNN)
+// ---- shared-memory staging by bulk copy (cp.async.bulk) with mbarriers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Bounded wait on a barrier phase; false when the budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+constexpr int kN2NWarps = 4;
+constexpr int kMetaCap = 256;  // list entries whose metadata a warp caches in shared memory
+
+struct __align__(16) N2NWarpSmem {
+  float ent_r2[kMetaCap];   // r_low^2 of each list entry
+  int ent_s0[kMetaCap];     // first child (global index) of the entry's source
+  int ent_cnt[kMetaCap];    // children of the entry's source
+  int ent_code[kMetaCap];   // image code of the source relative to the receiver (periodic)
+};
+
+// Image code of a source box relative to a receiver box in a periodic box:
+// bits 0-5 hold, per dimension, 0 (no shift), 1 (+L) or 2 (-L) when that image is
+// the minimum image for every pair of points of the two boxes; bit 6 = ambiguous.
+template <bool PER>
+__device__ __forceinline__ int image_code(const float* alo, const float* ahi, const float* blo,
+                                          const float* bhi, float L) {
+  if (!PER) return 0;
+  const float halfL = 0.5f * L;
+  int code = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float dlo = __fsub_rd(blo[d], ahi[d]);
+    const float dhi = __fsub_ru(bhi[d], alo[d]);
+    if (dlo >= -halfL && dhi <= halfL) {
+    } else if (dhi <= -halfL) {
+      code |= 1 << (2 * d);
+    } else if (dlo >= halfL) {
+      code |= 2 << (2 * d);
+    } else {
+      code |= 64;
+    }
+  }
+  return code;
+}
+
+// Box-box bounds with a fixed image: the source box is shifted by the code's
+// image (rounded outward) and the open-box formulas apply; ambiguous pairs use
+// the minimum over the images.
+template <bool PER, bool UP>
+__device__ __forceinline__ float box_bound2(const NodeRec& a, const NodeRec& b, int code, float L) {
+  if (PER && (code & 64)) {
+    return UP ? box_dup2<true>(a.lo, a.hi, b.lo, b.hi, L) : box_dlow2<true>(a.lo, a.hi, b.lo, b.hi, L);
+  }
+  float blo[3], bhi[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int c = PER ? (code >> (2 * d)) & 3 : 0;
+    const float sh = c == 1 ? L : (c == 2 ? -L : 0.0f);
+    blo[d] = c ? __fadd_rd(b.lo[d], sh) : b.lo[d];
+    bhi[d] = c ? __fadd_ru(b.hi[d], sh) : b.hi[d];
+  }
+  return UP ? box_dup2<false>(a.lo, a.hi, blo, bhi, L) : box_dlow2<false>(a.lo, a.hi, blo, bhi, L);
+}
+
+// Squared distance between box centres under the code's image (ordering only).
+template <bool PER>
+__device__ __forceinline__ float centre_d2(const NodeRec& a, const NodeRec& b, int code, float L) {
+  float s = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    float dd = 0.5f * (b.lo[d] + b.hi[d]) - 0.5f * (a.lo[d] + a.hi[d]);
+    if (PER) {
+      if (code & 64) dd -= L * rintf(dd / L);
+      else {
+        const int c = (code >> (2 * d)) & 3;
+        dd += c == 1 ? L : (c == 2 ? -L : 0.0f);
+      }
+    }
+    s = fmaf(dd, dd, s);
+  }
+  return s;
+}
+
+// One warp per receiving parent; G lanes per child split the candidates (the
+// children of the parent's source parents).  The list metadata (first child,
+// child count, r_low^2 and image code of each source) is gathered once per
+// parent, 32 entries at a time, into shared memory.
 template <int NR, bool PER>
-__global__ void __launch_bounds__(128) k_n2n_knn(const int32_t* __restrict__ spl_par,
-                                                 const uint2* __restrict__ ilo_par,
-                                                 const NodeRec* __restrict__ nodes,
-                                                 uint2* __restrict__ ilo_out, IEntry* arena,
-                                                 int par_plane, int k, float L, int64_t cap_ilist,
-                                                 int64_t ws_total, Meta* m) {
+__global__ void __launch_bounds__(32 * kN2NWarps) k_n2n_knn(const int32_t* __restrict__ spl_par,
+                                                            const uint2* __restrict__ ilo_par,
+                                                            const NodeRec* __restrict__ par_nodes,
+                                                            const NodeRec* __restrict__ nodes,
+                                                            uint2* __restrict__ ilo_out, IEntry* arena,
+                                                            int par_plane, int k, float L,
+                                                            int64_t cap_ilist, int64_t ws_total,
+                                                            Meta* m) {
+  __shared__ N2NWarpSmem S_all[kN2NWarps];
   if (warp_failed(m)) return;
-  const int64_t npar = m->n_nodes[par_plane];
   const int lane = lane_id();
+  N2NWarpSmem& S = S_all[warp_id()];
+  const int64_t npar = m->n_nodes[par_plane];
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t P = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; P < npar; P += nw) {
     const int c_begin = spl_par[P], c_end = spl_par[P + 1];
     const uint2 lo = ilo_par[P];
     const uint32_t e_off = lo.x, e_cnt = lo.y & ~kUnsortedBit;
     const bool sorted = (lo.y & kUnsortedBit) == 0;
+    // receiver box for image codes; the super level has no records (codes = ambiguous)
+    NodeRec pb;
+    const bool have_par = par_nodes != nullptr;
+    if (have_par) pb = par_nodes[P];
+    auto load_meta = [&](uint32_t e, float& r2, int& s0, int& cnt, int& code) {
+      const IEntry en = arena[e_off + e];
+      r2 = en.r2low;
+      s0 = spl_par[en.src];
+      cnt = spl_par[en.src + 1] - s0;
+      if (PER) {
+        if (have_par) {
+          const NodeRec sb = par_nodes[en.src];
+          code = image_code<PER>(pb.lo, pb.hi, sb.lo, sb.hi, L);
+        } else {
+          code = 64;
+        }
+      } else {
+        code = 0;
+      }
+    };
+    const uint32_t n_cached = min(e_cnt, (uint32_t)kMetaCap);
+    for (uint32_t e = lane; e < n_cached; e += 32) {
+      float r2;
+      int s0, cnt, code;
+      load_meta(e, r2, s0, cnt, code);
+      S.ent_r2[e] = r2;
+      S.ent_s0[e] = s0;
+      S.ent_cnt[e] = cnt;
+      S.ent_code[e] = code;
+    }
+    __syncwarp();
+    auto entry = [&](uint32_t e, float& r2, int& s0, int& cnt, int& code) {
+      if (e < (uint32_t)kMetaCap) {
+        r2 = S.ent_r2[e];
+        s0 = S.ent_s0[e];
+        cnt = S.ent_cnt[e];
+        code = S.ent_code[e];
+      } else {
+        load_meta(e, r2, s0, cnt, code);
+      }
+    };
+
     const int C = c_end - c_begin;
     int G = 1;
     while (G < 32 && 2 * G * C <= 32) G *= 2;
@@ -172,23 +335,23 @@ __global__ void __launch_bounds__(128) k_n2n_knn(const int32_t* __restrict__ spl
         me.count = 0;
         me.first = 0;
       }
-      // ---- FindRmax
+      // ---- FindRmax (Alg. 3)
       RHeap<NR> H;
       H.init();
       for (uint32_t e = 0; e < e_cnt; ++e) {
-        const IEntry en = arena[e_off + e];
-        const bool need = act && en.r2low < H.rad;
+        float r2;
+        int s0, cnt, code;
+        entry(e, r2, s0, cnt, code);
+        const bool need = act && r2 < H.rad;
         if (!__any_sync(kFull, need)) {
           if (sorted) break;
           continue;
         }
-        const int s0 = spl_par[en.src], s1 = spl_par[en.src + 1];
-        for (int jj = s0; jj < s1; jj += G) {
-          const int j = jj + sub;
-          if (need && j < s1) {
-            const NodeRec o = nodes[j];
-            const float r2 = box_dup2<PER>(me.lo, me.hi, o.lo, o.hi, L);
-            if (r2 < H.rad) H.insert(r2, o.count, k);
+        for (int j = sub; j < cnt; j += G) {
+          if (need) {
+            const NodeRec o = nodes[s0 + j];
+            const float u2 = box_bound2<PER, true>(me, o, code, L);
+            if (u2 < H.rad) H.insert(u2, o.count, k);
           }
         }
       }
@@ -209,65 +372,68 @@ __global__ void __launch_bounds__(128) k_n2n_knn(const int32_t* __restrict__ spl
       }
       const float R2 = __shfl_sync(kFull, H.rad, lane & ~(G - 1));
       // ---- Count
-      uint32_t cnt = 0;
+      uint32_t cnt_out = 0;
       for (uint32_t e = 0; e < e_cnt; ++e) {
-        const IEntry en = arena[e_off + e];
-        const bool need = act && en.r2low <= R2;
+        float r2;
+        int s0, cnt, code;
+        entry(e, r2, s0, cnt, code);
+        const bool need = act && r2 <= R2;
         if (!__any_sync(kFull, need)) {
           if (sorted) break;
           continue;
         }
-        const int s0 = spl_par[en.src], s1 = spl_par[en.src + 1];
-        for (int j = s0 + sub; j < s1; j += G) {
-          if (need) {
-            const NodeRec o = nodes[j];
-            cnt += box_dlow2<PER>(me.lo, me.hi, o.lo, o.hi, L) <= R2 ? 1u : 0u;
-          }
+        for (int j = sub; j < cnt; j += G) {
+          if (need) cnt_out += box_bound2<PER, false>(me, nodes[s0 + j], code, L) <= R2 ? 1u : 0u;
         }
       }
-      uint32_t tot = cnt;
+      uint32_t tot = cnt_out;
       for (int st = 1; st < G; st <<= 1) tot += __shfl_xor_sync(kFull, tot, st);
-      const uint32_t incl = warp_incl_scan_u(cnt);
-      const uint32_t excl = incl - cnt;
+      const uint32_t incl = warp_incl_scan_u(cnt_out);
+      const uint32_t excl = incl - cnt_out;
       const uint32_t wtot = __shfl_sync(kFull, incl, 31);
-      unsigned long long base = 0;
-      if (lane == 0 && wtot) base = atomicAdd(&m->arena_used, (unsigned long long)wtot);
-      base = __shfl_sync(kFull, base, 0);
-      const bool ok = base + wtot <= (unsigned long long)cap_ilist;
+      unsigned long long base_out = 0;
+      if (lane == 0 && wtot) base_out = atomicAdd(&m->arena_used, (unsigned long long)wtot);
+      base_out = __shfl_sync(kFull, base_out, 0);
+      const bool ok = base_out + wtot <= (unsigned long long)cap_ilist;
       if (!ok) {
         if (lane == 0) {
           set_error(m, JZT_ERR_CAPACITY, kStageWalk);
           atomicMax(reinterpret_cast<unsigned long long*>(&m->required_bytes),
-                    (unsigned long long)(ws_total + (int64_t)(base + wtot - cap_ilist) * (int64_t)sizeof(IEntry)));
+                    (unsigned long long)(ws_total + (int64_t)(base_out + wtot - cap_ilist) * (int64_t)sizeof(IEntry)));
         }
       } else {
         // ---- Insert
-        unsigned long long pos = base + excl;
+        unsigned long long pos = base_out + excl;
         for (uint32_t e = 0; e < e_cnt; ++e) {
-          const IEntry en = arena[e_off + e];
-          const bool need = act && en.r2low <= R2;
+          float r2;
+          int s0, cnt, code;
+          entry(e, r2, s0, cnt, code);
+          const bool need = act && r2 <= R2;
           if (!__any_sync(kFull, need)) {
             if (sorted) break;
             continue;
           }
-          const int s0 = spl_par[en.src], s1 = spl_par[en.src + 1];
-          for (int j = s0 + sub; j < s1; j += G) {
+          for (int j = sub; j < cnt; j += G) {
             if (need) {
-              const NodeRec o = nodes[j];
-              const float d2 = box_dlow2<PER>(me.lo, me.hi, o.lo, o.hi, L);
+              const NodeRec o = nodes[s0 + j];
+              const float d2 = box_bound2<PER, false>(me, o, code, L);
               if (d2 <= R2) {
-                IEntry w;
-                w.src = j;
-                w.r2low = d2;
-                arena[pos++] = w;
+                // packed for the list sort: bf16 of the centre distance^2 (high half)
+                // and of r_low^2 rounded down (low half)
+                const float c2 = centre_d2<PER>(me, o, code, L);
+                IEntry wr;
+                wr.src = s0 + j;
+                wr.r2low = __uint_as_float((__float_as_uint(c2) & 0xffff0000u) | (__float_as_uint(d2) >> 16));
+                arena[pos++] = wr;
               }
             }
           }
         }
       }
       const uint32_t gexcl = __shfl_sync(kFull, excl, lane & ~(G - 1));
-      if (act && sub == 0) ilo_out[cl] = ok ? make_uint2((uint32_t)(base + gexcl), tot) : make_uint2(0u, 0u);
+      if (act && sub == 0) ilo_out[cl] = ok ? make_uint2((uint32_t)(base_out + gexcl), tot) : make_uint2(0u, 0u);
     }
+    __syncwarp();  // cached metadata is rewritten for the next parent
   }
 }
 
@@ -314,40 +480,28 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&v)[E]) {
 
 // Order of a receiver's list: by the squared distance between node-box centres
 // (nearest first), so that the running k-th distance of a walk shrinks early;
-// ties by r_low^2, then by source index.  After sorting, every entry's r_low^2 is
-// replaced by the minimum r_low^2 of itself and all later entries (rounded down
-// to bf16 precision: still a lower bound), so "stop once r_low^2 exceeds the
-// threshold" stays exact along the list.
-template <int E, bool PER>
-__device__ __forceinline__ void sort_list(IEntry* list, uint32_t cnt, const NodeRec& me,
-                                          const NodeRec* __restrict__ src_nodes, float L) {
+// ties by r_low^2, then by source index.  The NodeToNode insert stored both keys
+// as bf16 halves of the r2low field.  After sorting, every entry's r_low^2 is
+// replaced by the minimum r_low^2 of itself and all later entries (bf16, rounded
+// down: still a lower bound), so "stop once r_low^2 exceeds the threshold" stays
+// exact along the list.  Lists too long to sort in registers are only unpacked
+// and flagged unsorted.
+template <int E>
+__device__ __forceinline__ void sort_list(IEntry* list, uint32_t cnt) {
   const int lane = lane_id();
   unsigned long long v[E];
-  float ca[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) ca[d] = 0.5f * (me.lo[d] + me.hi[d]);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const uint32_t i = lane * E + e;
     if (i < cnt) {
       const IEntry x = list[i];
-      const NodeRec o = src_nodes[x.src];
-      float c2 = 0.0f;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        float dd = 0.5f * (o.lo[d] + o.hi[d]) - ca[d];
-        if (PER) dd -= L * rintf(dd / L);
-        c2 = fmaf(dd, dd, c2);
-      }
-      const unsigned long long k16 = __float_as_uint(c2) >> 16;
-      const unsigned long long r16 = __float_as_uint(x.r2low) >> 16;  // truncation rounds down
-      v[e] = (k16 << 48) | (r16 << 32) | (uint32_t)x.src;
+      v[e] = ((unsigned long long)__float_as_uint(x.r2low) << 32) | (uint32_t)x.src;
     } else {
       v[e] = ~0ull;
     }
   }
   warp_bitonic<E>(v);
-  // suffix minimum of r16 (pads count as +inf)
+  // suffix minimum of the r_low^2 half (pads count as +inf)
   uint32_t r[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -362,7 +516,7 @@ __device__ __forceinline__ void sort_list(IEntry* list, uint32_t cnt, const Node
     const uint32_t t = __shfl_down_sync(kFull, tail, o);
     if (lane + o < 32) tail = min(tail, t);
   }
-  // tail now holds min over lanes >= lane; exclude this lane's own part
+  // tail holds the minimum over lanes >= lane; take the part after this lane
   uint32_t later = __shfl_down_sync(kFull, tail, 1);
   if (lane == 31) later = 0x7f80u;
 #pragma unroll
@@ -377,10 +531,7 @@ __device__ __forceinline__ void sort_list(IEntry* list, uint32_t cnt, const Node
   }
 }
 
-template <bool PER>
-__global__ void __launch_bounds__(128) k_sort_lists(uint2* ilo, IEntry* arena,
-                                                    const NodeRec* __restrict__ nodes, int plane,
-                                                    float L, Meta* m) {
+__global__ void __launch_bounds__(128) k_sort_lists(uint2* ilo, IEntry* arena, int plane, Meta* m) {
   if (warp_failed(m)) return;
   const int64_t nn = m->n_nodes[plane];
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -388,49 +539,22 @@ __global__ void __launch_bounds__(128) k_sort_lists(uint2* ilo, IEntry* arena,
     const uint2 lo = ilo[c];
     const uint32_t cnt = lo.y;
     IEntry* list = arena + lo.x;
-    if (cnt <= 1) continue;
-    const NodeRec me = nodes[c];
-    if (cnt <= 32) sort_list<1, PER>(list, cnt, me, nodes, L);
-    else if (cnt <= 64) sort_list<2, PER>(list, cnt, me, nodes, L);
-    else if (cnt <= 128) sort_list<4, PER>(list, cnt, me, nodes, L);
-    else if (cnt <= 256) sort_list<8, PER>(list, cnt, me, nodes, L);
-    else if (lane_id() == 0) ilo[c] = make_uint2(lo.x, cnt | kUnsortedBit);
+    if (cnt <= 32) sort_list<1>(list, cnt);
+    else if (cnt <= 64) sort_list<2>(list, cnt);
+    else if (cnt <= 128) sort_list<4>(list, cnt);
+    else if (cnt <= 256) sort_list<8>(list, cnt);
+    else {
+      for (uint32_t i = lane_id(); i < cnt; i += 32) {
+        IEntry x = list[i];
+        x.r2low = __uint_as_float(__float_as_uint(x.r2low) << 16);
+        list[i] = x;
+      }
+      if (lane_id() == 0) ilo[c] = make_uint2(lo.x, cnt | kUnsortedBit);
+    }
   }
 }
 
 // ------------------------------------------------------------------ LeafToLeaf (kNN)
-template <int KMAX>
-struct TopK {
-  float d[KMAX];
-  int i[KMAX];
-  __device__ __forceinline__ void init(int k) {
-#pragma unroll
-    for (int e = 0; e < KMAX; ++e) {
-      const bool pad = e < KMAX - k;  // front padding keeps the k-th entry last
-      d[e] = pad ? -INFINITY : INFINITY;
-      i[e] = pad ? -1 : INT_MAX;
-    }
-  }
-  __device__ __forceinline__ float thr_d() const { return d[KMAX - 1]; }
-  __device__ __forceinline__ int thr_i() const { return i[KMAX - 1]; }
-  __device__ __forceinline__ bool beats(float dd, int ii) const {
-    return dd < d[KMAX - 1] || (dd == d[KMAX - 1] && ii < i[KMAX - 1]);
-  }
-  // sorted insertion by (d, i); the last entry falls off
-  __device__ __forceinline__ void insert(float dd, int ii) {
-#pragma unroll
-    for (int e = 0; e < KMAX; ++e) {
-      const bool lt = dd < d[e] || (dd == d[e] && ii < i[e]);
-      const float td = d[e];
-      const int ti = i[e];
-      d[e] = lt ? dd : td;
-      i[e] = lt ? ii : ti;
-      dd = lt ? td : dd;
-      ii = lt ? ti : ii;
-    }
-  }
-};
-
 __device__ __forceinline__ float wrap1(float d, float L, float invL) {
   return d - L * rintf(d * invL);
 }
@@ -448,64 +572,99 @@ __device__ __forceinline__ float point_box_d2(float4 q, const NodeRec& b, float 
   return s * kLowSlack;
 }
 
-// ---- shared-memory staging by bulk copy (cp.async.bulk) with mbarriers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// Bounded wait on a stage barrier; false when the budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-constexpr int kQCap = 16;      // queued candidates per lane before a merge
+constexpr int kQCap = 8;       // queued candidates per lane before a merge
 constexpr int kL2LWarps = 4;
 constexpr int kStages = 4;     // source leaves in flight per warp
 constexpr int kUnroll = 4;     // source points per vote
 
+// Candidates are packed as (float32 bits of d2) << 32 | (original index + 1):
+// for d2 >= 0 the unsigned order of the key is the order by (d2, index), and 0
+// is below every real key (used to pad lists for k below the list size).
+constexpr unsigned long long kKeyInf = ~0ull;
+__device__ __forceinline__ unsigned long long pack_key(float d2, int idx) {
+  return ((unsigned long long)__float_as_uint(d2) << 32) | (uint32_t)(idx + 1);
+}
+
 struct __align__(16) L2LWarpSmem {
-  float4 pts[kStages][32];      // staged source leaves (<= 32 points each)
+  float4 pts[kStages][32];              // staged source leaves (<= 32 points each)
   uint64_t bar[kStages];
-  float qd[kQCap][32];
-  int qi[kQCap][32];
+  unsigned long long q[kQCap][32];      // per-lane candidate queue
 };
+
+__device__ __forceinline__ void cswap(unsigned long long& a, unsigned long long& b) {
+  const unsigned long long lo = a < b ? a : b, hi = a < b ? b : a;
+  a = lo;
+  b = hi;
+}
+
+// Sorted top-K of packed keys in registers (ascending; the first K-k slots hold
+// 0 so that the k-th best key is always the last one).  New keys are merged in
+// batches: the batch is sorted with a bitonic network, paired against the list
+// in reverse (which leaves a bitonic sequence holding the K smallest keys of
+// both), and a bitonic merge restores the order.  Branch-free, so lanes with
+// different numbers of new keys do not diverge.
+template <int K>
+struct RegTopK {
+  unsigned long long t[K];
+  __device__ __forceinline__ void init(int k) {
+#pragma unroll
+    for (int e = 0; e < K; ++e) t[e] = e < K - k ? 0ull : kKeyInf;
+  }
+  __device__ __forceinline__ float thr() const {
+    return t[K - 1] == kKeyInf ? INFINITY : __uint_as_float((uint32_t)(t[K - 1] >> 32));
+  }
+  template <int B>
+  __device__ __forceinline__ void merge(unsigned long long (&b)[B]) {
+    // sort the batch ascending
+#pragma unroll
+    for (int size = 2; size <= B; size <<= 1)
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1)
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+          const int j = i ^ stride;
+          if (j > i) {
+            if ((i & size) == 0) cswap(b[i], b[j]);
+            else cswap(b[j], b[i]);
+          }
+        }
+    // keep the K smallest of both lists: min against the reversed batch
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const int j = K - 1 - i;
+      if (j < B) t[i] = t[i] < b[j] ? t[i] : b[j];
+    }
+    // bitonic merge
+#pragma unroll
+    for (int stride = K >> 1; stride > 0; stride >>= 1)
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const int j = i ^ stride;
+        if (j > i) cswap(t[i], t[j]);
+      }
+  }
+};
+
+// Merge a lane's queued candidates into its top-k; returns the new k-th distance.
+template <int K>
+__device__ __forceinline__ float flush_queue(unsigned long long (*q)[32], RegTopK<K>& T, int lane,
+                                             int& qn, bool act, uint32_t& n_queued) {
+  unsigned long long b[kQCap];
+#pragma unroll
+  for (int t = 0; t < kQCap; ++t) b[t] = t < qn ? q[t][lane] : kKeyInf;
+  n_queued += qn;
+  qn = 0;
+  T.template merge<kQCap>(b);
+  return act ? T.thr() : -INFINITY;
+}
 
 // Per-leaf-pair distance mode (uniform over the warp): 0 plain, 1 fixed image
 // shift, 2 per-pair minimum image.
 template <bool PER>
-__device__ __forceinline__ int pair_mode(const NodeRec& A, float bl0, float bl1, float bl2, float bh0,
-                                         float bh1, float bh2, float L, float* sh) {
+__device__ __forceinline__ int pair_mode(const NodeRec& A, const float* blo, const float* bhi,
+                                         float L, float* sh) {
   if (!PER) return 0;
   const float halfL = 0.5f * L;
-  const float blo[3] = {bl0, bl1, bl2}, bhi[3] = {bh0, bh1, bh2};
   bool amb = false, any = false;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -543,13 +702,13 @@ __device__ __forceinline__ float pair_d2(const float4& p, const float4& q, const
 }
 
 // Scan one staged source leaf: every (query lane, source point) pair; distances
-// at or below the lane's k-th distance are queued, the queue is merged into the
-// top-k when any lane's queue is nearly full.
-template <int MODE, int KMAX>
+// at or below the lane's k-th distance are queued, and the queues are merged
+// into the lists when any lane's queue is nearly full.
+template <int MODE, int K>
 __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt, int G, int sub,
                                           const float4& qp, const float* sh, float L, float invL,
-                                          TopK<KMAX>& T, float& thr, int& qn, float (*qd)[32],
-                                          int (*qi)[32], int lane, bool act) {
+                                          float& thr, int& qn, unsigned long long (*q)[32],
+                                          RegTopK<K>& T, int lane, bool act, uint32_t& n_queued) {
   for (int j0 = 0; j0 < cnt; j0 += kUnroll * G) {
     float d2[kUnroll];
     int id[kUnroll];
@@ -561,27 +720,13 @@ __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt
       id[u] = __float_as_int(p.w);
       if (j >= 32) d2[u] = INFINITY;
     }
-    bool c = false;
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) c |= d2[u] <= thr;
-    if (__any_sync(kFull, c)) {
+    const float mn = fminf(fminf(d2[0], d2[1]), fminf(d2[2], d2[3]));
+    if (__any_sync(kFull, mn <= thr)) {
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
-        if (d2[u] <= thr) {
-          qd[qn][lane] = d2[u];
-          qi[qn][lane] = id[u];
-          ++qn;
-        }
+        if (d2[u] <= thr) q[qn++][lane] = pack_key(d2[u], id[u]);
       }
-      if (__any_sync(kFull, qn > kQCap - kUnroll)) {
-        for (int t = 0; t < qn; ++t) {
-          const float dd = qd[t][lane];
-          const int ii = qi[t][lane];
-          if (T.beats(dd, ii)) T.insert(dd, ii);
-        }
-        qn = 0;
-        thr = act ? T.thr_d() : -INFINITY;
-      }
+      if (__any_sync(kFull, qn > kQCap - kUnroll)) thr = flush_queue<K>(q, T, lane, qn, act, n_queued);
     }
   }
 }
@@ -589,7 +734,8 @@ __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt
 // One warp per query leaf.  Source leaves of the (sorted) interaction list are
 // staged into shared memory by bulk copies, kStages ahead of the computation;
 // the list metadata (source box and point range) is read 32 entries at a time,
-// one entry per lane.
+// one entry per lane.  Each query lane keeps its k best (d2, index) keys in a
+// sorted register list (RegTopK); its last key is the running k-th distance.
 template <int KMAX, bool PER>
 __global__ void __launch_bounds__(32 * kL2LWarps) k_l2l_knn(const float4* __restrict__ pts,
                                                            const NodeRec* __restrict__ leaves,
@@ -623,11 +769,13 @@ __global__ void __launch_bounds__(32 * kL2LWarps) k_l2l_knn(const float4* __rest
     const int qi = lane / G, sub = lane & (G - 1);
     const bool act = qi < q;
     const float4 qp = act ? pts[me.first + qi] : make_float4(0.f, 0.f, 0.f, 0.f);
-    TopK<KMAX> T;
+    RegTopK<KMAX> T;
     T.init(k);
-    float thr = act ? T.thr_d() : -INFINITY;
+    float thr = act ? INFINITY : -INFINITY;
     int qn = 0;
     unsigned long long pairs = 0;
+    unsigned long long st_examined = 0, st_scanned = 0;
+    uint32_t n_queued = 0;
     const uint2 lo = ilo[leaf];
     const uint32_t e_cnt = lo.y & ~kUnsortedBit;
     const bool sorted = (lo.y & kUnsortedBit) == 0;
@@ -647,12 +795,12 @@ __global__ void __launch_bounds__(32 * kL2LWarps) k_l2l_knn(const float4* __rest
       } else {
         sr.count = 0;
         sr.first = 0;
+        sr.lo[0] = sr.lo[1] = sr.lo[2] = sr.hi[0] = sr.hi[1] = sr.hi[2] = 0.0f;
       }
       uint32_t issued = 0, done = 0;
       auto issue = [&](uint32_t e) {
         const float r2 = __shfl_sync(kFull, en.r2low, e);
-        const bool reach = act && r2 <= thr;
-        if (sorted && !__any_sync(kFull, reach)) {
+        if (sorted && !__any_sync(kFull, act && r2 <= thr)) {
           stop = true;
           return;
         }
@@ -684,13 +832,14 @@ __global__ void __launch_bounds__(32 * kL2LWarps) k_l2l_knn(const float4* __rest
         }
         parity ^= 1u << st;
         ++done;
+        ++st_examined;
         const int cnt = __shfl_sync(kFull, sr.count, e);
         // pad the stage with far-away points so the unrolled scan needs no bounds
-        if (lane >= cnt) S.pts[st][lane] = make_float4(INFINITY, INFINITY, INFINITY, __int_as_float(INT_MAX));
+        if (lane >= cnt)
+          S.pts[st][lane] = make_float4(INFINITY, INFINITY, INFINITY, __int_as_float(INT_MAX));
         __syncwarp();
         const float r2 = __shfl_sync(kFull, en.r2low, e);
-        const bool reach = act && r2 <= thr;
-        bool skip = !__any_sync(kFull, reach);
+        bool skip = !__any_sync(kFull, act && r2 <= thr);
         if (skip && sorted) stop = true;
         float bl[3], bh[3];
 #pragma unroll
@@ -698,47 +847,65 @@ __global__ void __launch_bounds__(32 * kL2LWarps) k_l2l_knn(const float4* __rest
           bl[d] = __shfl_sync(kFull, sr.lo[d], e);
           bh[d] = __shfl_sync(kFull, sr.hi[d], e);
         }
+        float sh[3] = {0.0f, 0.0f, 0.0f};
+        int mode = 0;
         if (!skip) {
-          // point-to-box lower bound against this lane's threshold
+          // point-to-box lower bound against this lane's threshold, using the
+          // image chosen for the whole leaf pair (all three only when ambiguous)
+          mode = pair_mode<PER>(me, bl, bh, L, sh);
           float pb = 0.0f;
           const float qq[3] = {qp.x, qp.y, qp.z};
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            const float g = PER ? gap_rd_per(qq[d], qq[d], bl[d], bh[d], L) : gap_rd(qq[d], qq[d], bl[d], bh[d]);
+            float g;
+            if (PER && mode == 2) {
+              g = gap_rd_per(qq[d], qq[d], bl[d], bh[d], L);
+            } else {
+              const float lo_d = PER ? __fadd_rd(bl[d], sh[d]) : bl[d];
+              const float hi_d = PER ? __fadd_ru(bh[d], sh[d]) : bh[d];
+              g = fmaxf(0.0f, fmaxf(__fsub_rd(lo_d, qq[d]), __fsub_rd(qq[d], hi_d)));
+            }
             pb = __fmaf_rd(g, g, pb);
           }
           skip = !__any_sync(kFull, act && pb * kLowSlack <= thr);
         }
         if (!skip) {
           pairs += (unsigned long long)q * (unsigned long long)cnt;
-          float sh[3];
-          const int mode = pair_mode<PER>(me, bl[0], bl[1], bl[2], bh[0], bh[1], bh[2], L, sh);
-          if (mode == 0) scan_leaf<0, KMAX>(S.pts[st], cnt, G, sub, qp, sh, L, invL, T, thr, qn, S.qd, S.qi, lane, act);
-          else if (mode == 1) scan_leaf<1, KMAX>(S.pts[st], cnt, G, sub, qp, sh, L, invL, T, thr, qn, S.qd, S.qi, lane, act);
-          else scan_leaf<2, KMAX>(S.pts[st], cnt, G, sub, qp, sh, L, invL, T, thr, qn, S.qd, S.qi, lane, act);
+          ++st_scanned;
+          if (mode == 0)
+            scan_leaf<0, KMAX>(S.pts[st], cnt, G, sub, qp, sh, L, invL, thr, qn, S.q, T, lane, act, n_queued);
+          else if (mode == 1)
+            scan_leaf<1, KMAX>(S.pts[st], cnt, G, sub, qp, sh, L, invL, thr, qn, S.q, T, lane, act, n_queued);
+          else
+            scan_leaf<2, KMAX>(S.pts[st], cnt, G, sub, qp, sh, L, invL, thr, qn, S.q, T, lane, act, n_queued);
         }
         __syncwarp();
         if (!stop && issued < nb) issue(issued);
       }
     }
-    // merge what is still queued
-    for (int t = 0; t < qn; ++t) {
-      const float dd = S.qd[t][lane];
-      const int ii = S.qi[t][lane];
-      if (T.beats(dd, ii)) T.insert(dd, ii);
-    }
+    thr = flush_queue<KMAX>(S.q, T, lane, qn, act, n_queued);
     __syncwarp();
-    // merge the G partial lists of each query (butterfly; lists stay exact)
+    // merge the G partial lists of each query (butterfly over the sub-lanes)
     for (int st = 1; st < G; st <<= 1) {
-      TopK<KMAX> snap = T;  // the partner reads the pre-merge list
+      unsigned long long pb[KMAX];
 #pragma unroll
-      for (int e = 0; e < KMAX; ++e) {
-        const float dd = __shfl_xor_sync(kFull, snap.d[e], st);
-        const int ii = __shfl_xor_sync(kFull, snap.i[e], st);
-        if (act && dd >= 0.0f && T.beats(dd, ii)) T.insert(dd, ii);
-      }
+      for (int e = 0; e < KMAX; ++e) pb[e] = __shfl_xor_sync(kFull, T.t[e], st);
+      // the partner's pads (0) are not candidates: lift them out of the way
+#pragma unroll
+      for (int e = 0; e < KMAX; ++e) pb[e] = pb[e] == 0ull ? kKeyInf : pb[e];
+      T.template merge<KMAX>(pb);
     }
-    if (lane == 0 && pairs) atomicAdd(&m->knn_pairs, pairs);
+    if (lane == 0 && pairs) {
+      atomicAdd(&m->knn_pairs, pairs);
+      atomicAdd(&m->knn_stats[0], st_examined);
+      atomicAdd(&m->knn_stats[1], st_scanned);
+    }
+    {
+      unsigned long long a = n_queued;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
+      if (lane == 0) atomicAdd(&m->knn_stats[2], a);
+    }
     if (act && sub == 0 && !broken) {
       const int64_t row = order == 0 ? (int64_t)__float_as_int(qp.w) : (int64_t)(me.first + qi);
       int32_t* oi = out_idx + row * k;
@@ -746,13 +913,20 @@ __global__ void __launch_bounds__(32 * kL2LWarps) k_l2l_knn(const float4* __rest
 #pragma unroll
       for (int e = 0; e < KMAX; ++e) {
         if (e >= KMAX - k) {
-          oi[e - (KMAX - k)] = T.i[e];
-          od[e - (KMAX - k)] = T.d[e];
+          oi[e - (KMAX - k)] = (int32_t)(uint32_t)(T.t[e] & 0xffffffffull) - 1;
+          od[e - (KMAX - k)] = __uint_as_float((uint32_t)(T.t[e] >> 32));
         }
       }
     }
     __syncwarp();
   }
+}
+
+// Interaction-list entries written by one plane's NodeToNode (arena growth).
+__global__ void k_plane_mark(Meta* m, int plane, int end) {
+  if (threadIdx.x != 0) return;
+  if (!end) m->knn_plane_entries[plane] = m->arena_used;
+  else m->knn_plane_entries[plane] = m->arena_used - m->knn_plane_entries[plane];
 }
 
 __global__ void k_walk_peak(Meta* m) {
@@ -770,8 +944,9 @@ template <int NR, bool PER>
 void n2n_knn_plane(const Layout& L, char* ws, int p, int k, float pl, cudaStream_t s) {
   Meta* m = at<Meta>(ws, L.meta);
   const int sms = 152;
-  k_n2n_knn<NR, PER><<<grid_for(L.cap_nodes[p + 1] * 32, 128, sms * 16), 128, 0, s>>>(
-      at<int32_t>(ws, L.spl[p + 1]), at<uint2>(ws, L.ilo[p + 1]), at<NodeRec>(ws, L.nodes[p]),
+  const NodeRec* par_nodes = (p + 1 < L.n_planes) ? at<NodeRec>(ws, L.nodes[p + 1]) : nullptr;
+  k_n2n_knn<NR, PER><<<grid_for(L.cap_nodes[p + 1] * 32, 32 * kN2NWarps, sms * 16), 32 * kN2NWarps, 0, s>>>(
+      at<int32_t>(ws, L.spl[p + 1]), at<uint2>(ws, L.ilo[p + 1]), par_nodes, at<NodeRec>(ws, L.nodes[p]),
       at<uint2>(ws, L.ilo[p]), at<IEntry>(ws, L.arena), p + 1, k, pl, L.cap_ilist,
       (int64_t)L.total, m); note_launch();
 }
@@ -800,13 +975,15 @@ void knn_all(const Layout& L, char* ws, float pl, int k, int order, int32_t* idx
   prof_end(kPhKnnTop, s);
   for (int p = P - 1; p >= 0; --p) {
     prof_begin(kPhKnnN2N, s);
+    k_plane_mark<<<1, 32, 0, s>>>(m, p, 0); note_launch();
     if (L.heap <= 4) n2n_knn_plane<4, PER>(L, ws, p, k, pl, s);
     else if (L.heap <= 8) n2n_knn_plane<8, PER>(L, ws, p, k, pl, s);
     else n2n_knn_plane<16, PER>(L, ws, p, k, pl, s);
+    k_plane_mark<<<1, 32, 0, s>>>(m, p, 1); note_launch();
     prof_end(kPhKnnN2N, s);
     prof_begin(kPhKnnSort, s);
-    k_sort_lists<PER><<<grid_for(L.cap_nodes[p] * 32, 128, sms * 16), 128, 0, s>>>(
-        at<uint2>(ws, L.ilo[p]), at<IEntry>(ws, L.arena), at<NodeRec>(ws, L.nodes[p]), p, pl, m); note_launch();
+    k_sort_lists<<<grid_for(L.cap_nodes[p] * 32, 128, sms * 16), 128, 0, s>>>(
+        at<uint2>(ws, L.ilo[p]), at<IEntry>(ws, L.arena), p, m); note_launch();
     prof_end(kPhKnnSort, s);
   }
   prof_begin(kPhKnnL2L, s);
