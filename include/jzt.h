@@ -149,6 +149,24 @@ int jzt_tree_plane(const jzt_tree *t, int p, int64_t cap, int64_t *n_nodes,
 
 void jzt_tree_free(jzt_tree *t);
 
+/* Allocation-free form of jzt_knn (the paper has no counterpart: this is for
+ * callers that may not allocate device memory, e.g. inside a framework that owns
+ * all device allocations, or during stream capture).  Same results as jzt_knn
+ * (rows in input order), but the scratch space is a fixed 16 MiB device array
+ * inside the library rather than a caller workspace; the caller still owns
+ * d_xyz, d_idx and d_dist2.  Limits: 1 <= N <= 65536, 1 <= k <= min(32, N);
+ * larger sizes return JZT_ERR_INVALID with a message naming the limit.  Calls no
+ * allocator.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the one array per device: calls that overlap on the GPU (on
+ * different streams or threads) race and must be serialised by the caller; each
+ * call re-initialises what it needs, the rest keeps the previous call's data.
+ * info: NULL to return after enqueueing the work; otherwise the call
+ * synchronises `stream` and fills *info like jzt_status (device-side errors are
+ * then returned as the call's result). */
+int jzt_knn_noalloc(const float *d_xyz, int64_t n, int k, float periodic_L,
+                    int32_t *d_idx, float *d_dist2, void *stream, jzt_status_info *info);
+
 /* Instrumentation (no counterpart in the paper; used to measure the kernels).
  * jzt_profile_enable(1) makes every later call record a CUDA event pair on its
  * own stream around each kernel phase (phase names: jzt_profile_phase_name).

@@ -39,7 +39,8 @@ _NAMES = {0: "ok", -1: "invalid", -2: "unsupported", -3: "cuda", -4: "workspace"
 # Every entry point declared in include/jzt.h.
 SYMBOLS = ("jzt_workspace_bytes", "jzt_build", "jzt_tree_knn", "jzt_tree_fof", "jzt_knn", "jzt_fof",
            "jzt_status", "jzt_tree_arrays", "jzt_tree_plane", "jzt_tree_free", "jzt_last_error",
-           "jzt_version", "jzt_profile_enable", "jzt_profile_read", "jzt_profile_phase_name")
+           "jzt_version", "jzt_profile_enable", "jzt_profile_read", "jzt_profile_phase_name",
+           "jzt_knn_noalloc")
 
 
 class JztError(RuntimeError):
@@ -87,6 +88,8 @@ def _load():
     lib.jzt_profile_read.restype = ctypes.c_int
     lib.jzt_profile_phase_name.argtypes = [ctypes.c_int]
     lib.jzt_profile_phase_name.restype = ctypes.c_char_p
+    lib.jzt_knn_noalloc.argtypes = [vp, i64, ctypes.c_int, f32, vp, vp, vp, ctypes.POINTER(StatusInfo)]
+    lib.jzt_knn_noalloc.restype = ctypes.c_int
     lib.jzt_tree_free.argtypes = [vp]
     lib.jzt_tree_free.restype = None
     lib.jzt_last_error.restype = ctypes.c_char_p

@@ -1,0 +1,97 @@
+// Allocation-free kNN entry point.
+//
+// Some callers cannot allocate device memory at all: code that runs inside a
+// framework which owns every device allocation (and forbids cudaMalloc behind
+// its back), code called while a stream is being captured into a CUDA graph
+// (where a cudaMalloc would break the capture), or embedded and real-time users
+// that must not hit the allocator on their call path.  For them this file
+// provides jzt_knn_noalloc: the same build + kNN walk as jzt_knn, with its
+// scratch space taken from one fixed device array compiled into the library
+// instead of a caller-provided workspace.  The caller still owns the input and
+// output buffers.
+//
+// The array is g_noalloc_ws below (kNoAllocBytes, 16 MiB).  Every GPU that loads
+// the library holds it until the process exits.  In host code its name is only a
+// host-side stand-in for the device symbol, so its device address is looked up
+// with cudaGetSymbolAddress, once per device, with that device current, and that
+// address is what the kernels receive.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+
+namespace jzt {
+
+int fail_msg(int code, const std::string& msg);  // api.cu: sets jzt_last_error
+
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(16) << 20;  // 16 MiB of scratch per device
+constexpr int64_t kNoAllocMaxN = 65536;               // largest N the scratch holds (k <= 32)
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocBytes];
+
+std::mutex g_mu;
+void* g_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_ws on the current device (looked up on the
+// first call made on that device).
+int scratch_address(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_msg(JZT_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail_msg(JZT_ERR_UNSUPPORTED, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+    if (e != cudaSuccess || !p)
+      return fail_msg(JZT_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    g_addr[dev] = p;
+  }
+  *out = g_addr[dev];
+  return JZT_OK;
+}
+
+}  // namespace
+}  // namespace jzt
+
+using namespace jzt;
+
+extern "C" int jzt_knn_noalloc(const float* d_xyz, int64_t n, int k, float periodic_L, int32_t* d_idx,
+                               float* d_dist2, void* stream, jzt_status_info* info) {
+  if (!d_xyz || !d_idx || !d_dist2) return fail_msg(JZT_ERR_INVALID, "null device pointer");
+  if (reinterpret_cast<uintptr_t>(d_xyz) & 3u) return fail_msg(JZT_ERR_INVALID, "d_xyz must be 4-byte aligned");
+  if (n < 1 || n > kNoAllocMaxN)
+    return fail_msg(JZT_ERR_INVALID, "jzt_knn_noalloc handles 1 <= N <= " + std::to_string(kNoAllocMaxN) +
+                                         " points (got " + std::to_string(n) + "); use jzt_knn with a workspace");
+  if (k < 1 || (int64_t)k > n) return fail_msg(JZT_ERR_INVALID, "k must satisfy 1 <= k <= N");
+  if (k > kMaxK) return fail_msg(JZT_ERR_UNSUPPORTED, "k > 32 is not supported");
+  if (!std::isfinite(periodic_L)) return fail_msg(JZT_ERR_INVALID, "periodic_L must be finite");
+  Params P;
+  const char* why = nullptr;
+  if (int e = resolve_params(nullptr, &P, &why)) return fail_msg(e, why);
+  Layout need;
+  compute_layout(n, P, k, 0, &need);
+  if (need.total > kNoAllocBytes)
+    return fail_msg(JZT_ERR_INVALID, "problem needs " + std::to_string(need.total) + " bytes of scratch, the " +
+                                         "built-in array holds " + std::to_string(kNoAllocBytes));
+  void* ws = nullptr;
+  if (int e = scratch_address(&ws)) return e;
+  Layout L;
+  compute_layout(n, P, 0, kNoAllocBytes, &L);
+  const float pl = periodic_L > 0.0f ? periodic_L : 0.0f;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // Each call starts by re-initialising the status block, counters and look-back
+  // tables it uses; nothing else in the array needs to start at zero.
+  launch_build(d_xyz, n, pl, L, static_cast<char*>(ws), s);
+  launch_knn(L, static_cast<char*>(ws), pl, k, 0, d_idx, d_dist2, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_msg(JZT_ERR_CUDA, std::string("jzt_knn_noalloc launch: ") + cudaGetErrorString(e));
+  if (info) return jzt_status(ws, stream, info);
+  return JZT_OK;
+}
