@@ -62,9 +62,11 @@ def _load():
         lib.oracle_fof_brute.argtypes = [f32p, ctypes.c_int64, ctypes.c_double, ctypes.c_double, i32p]
         lib.oracle_fof_cells.argtypes = [f32p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, i32p, ctypes.c_int]
+        lib.oracle_fof_cells2.argtypes = [f32p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, i32p, i32p, ctypes.c_int]
         lib.oracle_num_threads.argtypes = [ctypes.c_int]
         for f in (lib.oracle_knn_brute, lib.oracle_knn_cells, lib.oracle_fof_brute,
-                  lib.oracle_fof_cells, lib.oracle_num_threads):
+                  lib.oracle_fof_cells, lib.oracle_fof_cells2, lib.oracle_num_threads):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -136,12 +138,21 @@ def fof_cells(xyz, b, periodic_L=0.0, rel=0.0, threads=0):
     return lab
 
 
-def fof_bracket(xyz, b, periodic_L=0.0, rel=1e-6, cells=None):
+def fof_bracket(xyz, b, periodic_L=0.0, rel=1e-6, cells=None, threads=0):
     """(labels at b^2(1-rel), labels at b^2(1+rel)): the strict and loose link graphs."""
     if cells is None:
         cells = np.asarray(xyz).shape[0] > 20000
-    f = fof_cells if cells else fof_brute
-    return f(xyz, b, periodic_L, -rel), f(xyz, b, periodic_L, rel)
+    if not cells:
+        return fof_brute(xyz, b, periodic_L, -rel), fof_brute(xyz, b, periodic_L, rel)
+    x = np.ascontiguousarray(xyz, dtype=np.float32)
+    la = np.empty(x.shape[0], dtype=np.int32)
+    lb = np.empty(x.shape[0], dtype=np.int32)
+    rc = _load().oracle_fof_cells2(_ptr(x, ctypes.c_float), x.shape[0], link_b2(b, -rel), link_b2(b, rel),
+                                   float(periodic_L), _ptr(la, ctypes.c_int32), _ptr(lb, ctypes.c_int32),
+                                   int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle FoF (cells) failed (rc={rc})")
+    return la, lb
 
 
 # ------------------------------------------------------------------ tree (Sec. II)

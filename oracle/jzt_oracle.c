@@ -323,19 +323,16 @@ int oracle_knn_cells(const float *xyz, int64_t n, int k, double L,
 }
 
 /* --------------------------------------------------------- cell-list FoF
- * Cells of side w <= b/sqrt(3)*(1-1e-9): the diagonal of a cell is below b, so
- * all points sharing a cell are pairwise linked (each cell is a clique).  A
- * linked pair is at most R = floor(b/w)+1 cells apart per dimension, so the
- * FoF components are the connected components of the cell graph whose edges
- * join cells (at offsets within +-R) that hold at least one linked pair.  The
- * occupied cells live in an open-addressing hash table.  Edge detection runs
- * in parallel (it only reads); the unions are applied sequentially. */
-typedef struct {
-    int64_t key;    /* linear cell id, -1 = empty slot */
-    int64_t first;  /* offset of the cell's points in the bucketed order */
-    int64_t count;
-} slot_t;
-
+ * Cells of side w <= b_a/sqrt(3)*(1-1e-9): the diagonal of a cell is below b_a,
+ * so all points sharing a cell are pairwise linked (each cell is a clique) for
+ * both thresholds b2_a <= b2_b.  A pair within sqrt(b2_b) is at most
+ * R = floor(sqrt(b2_b)/w) + 1 cells apart per dimension, so the FoF components of
+ * each graph are the connected components of the cell graph whose edges join
+ * cells (at offsets within +-R) holding at least one pair linked in that graph.
+ * Points are bucketed by cell with an LSD radix sort of the cell keys; cells are
+ * then grouped in rows of equal (cx, cy), and each row finds its neighbouring
+ * rows once through a hash table of rows.  Edge detection runs in parallel over
+ * rows (it only reads); the unions are applied sequentially. */
 static uint64_t mix64(uint64_t x)
 {
     x ^= x >> 33;
@@ -346,7 +343,13 @@ static uint64_t mix64(uint64_t x)
     return x;
 }
 
-static int64_t hash_find(const slot_t *tab, uint64_t mask, int64_t key)
+typedef struct {
+    int64_t key;    /* row id cx*gy + cy, -1 = empty slot */
+    int64_t first;  /* first cell of the row */
+    int64_t last;   /* one past the last cell */
+} row_slot_t;
+
+static int64_t row_find(const row_slot_t *tab, uint64_t mask, int64_t key)
 {
     uint64_t h = mix64((uint64_t)key) & mask;
     for (;;) {
@@ -358,25 +361,72 @@ static int64_t hash_find(const slot_t *tab, uint64_t mask, int64_t key)
     }
 }
 
-static int cmp_i64pair(const void *a, const void *b)
+/* stable LSD radix sort of (key, index) pairs on the low `bits` bits */
+static int radix_pairs(int64_t *key, int64_t *idx, int64_t n, int bits)
 {
-    const int64_t *x = (const int64_t *)a, *y = (const int64_t *)b;
-    if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
-    if (x[1] != y[1]) return x[1] < y[1] ? -1 : 1;
+    int64_t *k2 = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *i2 = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *cnt = (int64_t *)malloc((1 << 16) * sizeof(int64_t));
+    if (!k2 || !i2 || !cnt) {
+        free(k2); free(i2); free(cnt);
+        return -2;
+    }
+    for (int sh = 0; sh < bits; sh += 16) {
+        memset(cnt, 0, (1 << 16) * sizeof(int64_t));
+        for (int64_t i = 0; i < n; ++i)
+            cnt[((uint64_t)key[i] >> sh) & 0xffff]++;
+        int64_t run = 0;
+        for (int d = 0; d < (1 << 16); ++d) {
+            int64_t c = cnt[d];
+            cnt[d] = run;
+            run += c;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t pos = cnt[((uint64_t)key[i] >> sh) & 0xffff]++;
+            k2[pos] = key[i];
+            i2[pos] = idx[i];
+        }
+        memcpy(key, k2, (size_t)n * sizeof(int64_t));
+        memcpy(idx, i2, (size_t)n * sizeof(int64_t));
+    }
+    free(k2); free(i2); free(cnt);
     return 0;
 }
 
-int oracle_fof_cells(const float *xyz, int64_t n, double b, double b2, double L,
-                     int32_t *labels, int nthreads)
+typedef struct {
+    int64_t *e;   /* pairs (a, b, flag) */
+    int64_t n, cap;
+} edges_t;
+
+static int edge_push(edges_t *E, int64_t a, int64_t b, int64_t flag)
 {
-    if (n < 1 || !(b > 0.0))
+    if (E->n == E->cap) {
+        int64_t nc = E->cap ? 2 * E->cap : 4096;
+        int64_t *ne = (int64_t *)realloc(E->e, (size_t)nc * 3 * sizeof(int64_t));
+        if (!ne)
+            return -2;
+        E->e = ne;
+        E->cap = nc;
+    }
+    E->e[3 * E->n] = a;
+    E->e[3 * E->n + 1] = b;
+    E->e[3 * E->n + 2] = flag;
+    E->n++;
+    return 0;
+}
+
+/* labels_a: FoF at b2_a, labels_b: FoF at b2_b (b2_a <= b2_b); labels_b may be NULL */
+int oracle_fof_cells2(const float *xyz, int64_t n, double b2_a, double b2_b, double L,
+                      int32_t *labels_a, int32_t *labels_b, int nthreads)
+{
+    if (n < 1 || !(b2_a > 0.0) || b2_b < b2_a)
         return -1;
     set_threads(nthreads);
     double lo[3], hi[3];
     grid_box(xyz, n, L, lo, hi);
     grid_t g;
     g.L = L;
-    const double w0 = b / sqrt(3.0) * (1.0 - 1e-9);
+    const double w0 = sqrt(b2_a) / sqrt(3.0) * (1.0 - 1e-9);
     double wmin = w0;
     for (int c = 0; c < 3; ++c) {
         g.lo[c] = lo[c];
@@ -392,169 +442,190 @@ int oracle_fof_cells(const float *xyz, int64_t n, double b, double b2, double L,
         if (g.w[c] < wmin) wmin = g.w[c];
     }
     /* a linked pair is at most R cells apart in every dimension */
-    const int64_t R = (int64_t)floor(b / wmin) + 1;
-    const int64_t nnb = (2 * R + 1) * (2 * R + 1) * (2 * R + 1);
-    /* bucket points by cell: sort (cell id, index) pairs */
-    int64_t *pairs = (int64_t *)malloc((size_t)n * 2 * sizeof(int64_t));
-    if (!pairs)
+    const int64_t R = (int64_t)floor(sqrt(b2_b) / wmin) + 1;
+    int key_bits = 0;
+    while (key_bits < 63 && ((uint64_t)1 << key_bits) < (uint64_t)(g.g[0] * g.g[1] * g.g[2]))
+        ++key_bits;
+    int64_t *key = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *pt = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *p = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *q = labels_b ? (int64_t *)malloc((size_t)n * sizeof(int64_t)) : NULL;
+    if (!key || !pt || !p || (labels_b && !q)) {
+        free(key); free(pt); free(p); free(q);
         return -2;
+    }
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         int64_t cx = cell_coord(&g, xyz[3 * i + 0], 0);
         int64_t cy = cell_coord(&g, xyz[3 * i + 1], 1);
         int64_t cz = cell_coord(&g, xyz[3 * i + 2], 2);
-        pairs[2 * i] = (cx * g.g[1] + cy) * g.g[2] + cz;
-        pairs[2 * i + 1] = i;
+        key[i] = (cx * g.g[1] + cy) * g.g[2] + cz;
+        pt[i] = i;
     }
-    qsort(pairs, (size_t)n, 2 * sizeof(int64_t), cmp_i64pair);
-    int64_t ncell = 0;
-    for (int64_t t = 0; t < n; ++t)
-        if (t == 0 || pairs[2 * t] != pairs[2 * t - 2])
-            ++ncell;
-    uint64_t cap = 1;
-    while (cap < (uint64_t)ncell * 2)
-        cap <<= 1;
-    uint64_t mask = cap - 1;
-    slot_t *tab = (slot_t *)malloc(cap * sizeof(slot_t));
-    int64_t *cells = (int64_t *)malloc((size_t)ncell * sizeof(int64_t)); /* slot of each cell */
-    int64_t *p = (int64_t *)malloc((size_t)n * sizeof(int64_t));
-    if (!tab || !cells || !p) {
-        free(pairs); free(tab); free(cells); free(p);
+    if (radix_pairs(key, pt, n, key_bits)) {
+        free(key); free(pt); free(p); free(q);
         return -2;
+    }
+    /* cells (runs of equal keys) and rows (runs of equal key / gz) */
+    int64_t ncell = 0, nrow = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        if (t == 0 || key[t] != key[t - 1]) ++ncell;
+        if (t == 0 || key[t] / g.g[2] != key[t - 1] / g.g[2]) ++nrow;
+    }
+    int64_t *cfirst = (int64_t *)malloc((size_t)(ncell + 1) * sizeof(int64_t));
+    int64_t *ckey = (int64_t *)malloc((size_t)ncell * sizeof(int64_t));
+    int64_t *rcell = (int64_t *)malloc((size_t)(nrow + 1) * sizeof(int64_t));
+    uint64_t cap = 1;
+    while (cap < (uint64_t)nrow * 2) cap <<= 1;
+    const uint64_t mask = cap - 1;
+    row_slot_t *rows = (row_slot_t *)malloc(cap * sizeof(row_slot_t));
+    if (!cfirst || !ckey || !rcell || !rows) {
+        free(key); free(pt); free(p); free(q); free(cfirst); free(ckey); free(rcell); free(rows);
+        return -2;
+    }
+    {
+        int64_t c = -1, r = -1;
+        for (int64_t t = 0; t < n; ++t) {
+            if (t == 0 || key[t] != key[t - 1]) {
+                ++c;
+                cfirst[c] = t;
+                ckey[c] = key[t];
+                if (c == 0 || ckey[c] / g.g[2] != ckey[c - 1] / g.g[2])
+                    rcell[++r] = c;
+            }
+        }
+        cfirst[ncell] = n;
+        rcell[nrow] = ncell;
     }
     for (uint64_t h = 0; h < cap; ++h)
-        tab[h].key = -1;
-    {
-        int64_t c = -1;
-        for (int64_t t = 0; t < n; ++t) {
-            int64_t key = pairs[2 * t];
-            if (t == 0 || key != pairs[2 * t - 2]) {
-                uint64_t h = mix64((uint64_t)key) & mask;
-                while (tab[h].key >= 0)
-                    h = (h + 1) & mask;
-                tab[h].key = key;
-                tab[h].first = t;
-                tab[h].count = 0;
-                cells[++c] = (int64_t)h;
-            }
-            tab[cells[c]].count++;
+        rows[h].key = -1;
+    for (int64_t r = 0; r < nrow; ++r) {
+        int64_t rk = ckey[rcell[r]] / g.g[2];
+        uint64_t h = mix64((uint64_t)rk) & mask;
+        while (rows[h].key >= 0)
+            h = (h + 1) & mask;
+        rows[h].key = rk;
+        rows[h].first = rcell[r];
+        rows[h].last = rcell[r + 1];
+    }
+    /* union-find; first link each cell's clique to its first member */
+    for (int64_t i = 0; i < n; ++i) {
+        p[i] = i;
+        if (q) q[i] = i;
+    }
+    for (int64_t c = 0; c < ncell; ++c) {
+        int64_t head = pt[cfirst[c]];
+        for (int64_t t = cfirst[c] + 1; t < cfirst[c + 1]; ++t) {
+            uf_union(p, head, pt[t]);
+            if (q) uf_union(q, head, pt[t]);
         }
     }
-    /* union-find over points; first link each cell's clique to its smallest member
-     * (the bucketed order keeps indices ascending within a cell) */
-    for (int64_t i = 0; i < n; ++i)
-        p[i] = i;
-    for (int64_t c = 0; c < ncell; ++c) {
-        const slot_t *s = &tab[cells[c]];
-        int64_t head = pairs[2 * s->first + 1];
-        for (int64_t t = 1; t < s->count; ++t)
-            uf_union(p, head, pairs[2 * (s->first + t) + 1]);
-    }
-    /* cell-cell edges (each unordered pair once: the neighbour's key must be larger) */
     int nth = set_threads(0);
-    int64_t **edges = (int64_t **)calloc((size_t)nth, sizeof(int64_t *));
-    int64_t *ecount = (int64_t *)calloc((size_t)nth, sizeof(int64_t));
-    int64_t *ecap = (int64_t *)calloc((size_t)nth, sizeof(int64_t));
+    edges_t *E = (edges_t *)calloc((size_t)nth, sizeof(edges_t));
     int failed = 0;
-    int64_t **seenbuf = (int64_t **)calloc((size_t)nth, sizeof(int64_t *));
-    for (int t = 0; t < nth; ++t) {
-        seenbuf[t] = (int64_t *)malloc((size_t)nnb * sizeof(int64_t));
-        if (!seenbuf[t])
-            failed = 1;
-    }
-    if (failed) {
-        for (int t = 0; t < nth; ++t)
-            free(seenbuf[t]);
-        free(seenbuf); free(edges); free(ecount); free(ecap);
-        free(pairs); free(tab); free(cells); free(p);
-        return -2;
-    }
+    const int64_t nnb = (2 * R + 1) * (2 * R + 1);
 #pragma omp parallel
     {
         int tid = 0;
 #ifdef _OPENMP
         tid = omp_get_thread_num();
 #endif
-#pragma omp for schedule(dynamic, 256)
-        for (int64_t c = 0; c < ncell; ++c) {
-            const slot_t *sa = &tab[cells[c]];
-            int64_t key = sa->key;
-            int64_t cz = key % g.g[2];
-            int64_t cy = (key / g.g[2]) % g.g[1];
-            int64_t cx = key / (g.g[2] * g.g[1]);
-            int64_t *seen = seenbuf[tid];
-            int64_t nseen = 0;
+        int64_t *nb_first = (int64_t *)malloc((size_t)nnb * sizeof(int64_t));
+        int64_t *nb_last = (int64_t *)malloc((size_t)nnb * sizeof(int64_t));
+        int64_t *nb_row = (int64_t *)malloc((size_t)nnb * sizeof(int64_t));
+        if (!nb_first || !nb_last || !nb_row)
+            failed = 1;
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t r = 0; r < nrow; ++r) {
+            if (failed)
+                continue;
+            const int64_t rk = ckey[rcell[r]] / g.g[2];
+            const int64_t cx = rk / g.g[1], cy = rk % g.g[1];
+            /* neighbouring rows, each once (periodic wrap may repeat them) */
+            int64_t nn = 0;
             for (int64_t dx = -R; dx <= R; ++dx)
-                for (int64_t dy = -R; dy <= R; ++dy)
-                    for (int64_t dz = -R; dz <= R; ++dz) {
-                        int64_t o[3] = {cx + dx, cy + dy, cz + dz};
-                        int ok = 1;
-                        for (int d = 0; d < 3; ++d) {
-                            if (L > 0.0)
-                                o[d] = ((o[d] % g.g[d]) + g.g[d]) % g.g[d];
-                            else if (o[d] < 0 || o[d] >= g.g[d])
-                                ok = 0;
+                for (int64_t dy = -R; dy <= R; ++dy) {
+                    int64_t ox = cx + dx, oy = cy + dy;
+                    if (L > 0.0) {
+                        ox = ((ox % g.g[0]) + g.g[0]) % g.g[0];
+                        oy = ((oy % g.g[1]) + g.g[1]) % g.g[1];
+                    } else if (ox < 0 || ox >= g.g[0] || oy < 0 || oy >= g.g[1]) {
+                        continue;
+                    }
+                    int64_t ork = ox * g.g[1] + oy;
+                    int dup = 0;
+                    for (int64_t u = 0; u < nn; ++u)
+                        dup |= (nb_row[u] == ork);
+                    if (dup)
+                        continue;
+                    int64_t h = row_find(rows, mask, ork);
+                    if (h < 0)
+                        continue;
+                    nb_row[nn] = ork;
+                    nb_first[nn] = rows[h].first;
+                    nb_last[nn] = rows[h].last;
+                    ++nn;
+                }
+            for (int64_t ca = rcell[r]; ca < rcell[r + 1]; ++ca) {
+                const int64_t cz = ckey[ca] % g.g[2];
+                for (int64_t u = 0; u < nn; ++u) {
+                    for (int64_t cb = nb_first[u]; cb < nb_last[u]; ++cb) {
+                        if (ckey[cb] <= ckey[ca])
+                            continue; /* each unordered cell pair once */
+                        int64_t dz = ckey[cb] % g.g[2] - cz;
+                        if (L > 0.0) {
+                            dz = ((dz % g.g[2]) + g.g[2]) % g.g[2];
+                            if (dz > g.g[2] - dz) dz = g.g[2] - dz;
+                        } else if (dz < 0) {
+                            dz = -dz;
                         }
-                        if (!ok)
+                        if (dz > R)
                             continue;
-                        int64_t nkey = (o[0] * g.g[1] + o[1]) * g.g[2] + o[2];
-                        if (nkey <= key)
-                            continue;
-                        int dup = 0;
-                        for (int64_t u = 0; u < nseen; ++u)
-                            dup |= (seen[u] == nkey);
-                        if (dup)
-                            continue;
-                        seen[nseen++] = nkey;
-                        int64_t hb = hash_find(tab, mask, nkey);
-                        if (hb < 0)
-                            continue;
-                        const slot_t *sb = &tab[hb];
-                        int linked = 0;
-                        for (int64_t ta = 0; ta < sa->count && !linked; ++ta) {
-                            int64_t ia = pairs[2 * (sa->first + ta) + 1];
-                            for (int64_t tb = 0; tb < sb->count; ++tb) {
-                                int64_t ib = pairs[2 * (sb->first + tb) + 1];
-                                if (pair_d2(xyz + 3 * ia, xyz + 3 * ib, L) <= b2) {
-                                    linked = 1;
+                        int la = 0, lb = 0;
+                        for (int64_t ta = cfirst[ca]; ta < cfirst[ca + 1] && !la; ++ta) {
+                            const int64_t ia = pt[ta];
+                            for (int64_t tb = cfirst[cb]; tb < cfirst[cb + 1]; ++tb) {
+                                const double d2 = pair_d2(xyz + 3 * ia, xyz + 3 * pt[tb], L);
+                                if (d2 <= b2_a) {
+                                    la = 1;
                                     break;
                                 }
+                                if (d2 <= b2_b)
+                                    lb = 1;
                             }
                         }
-                        if (linked) {
-                            if (ecount[tid] == ecap[tid]) {
-                                int64_t nc = ecap[tid] ? 2 * ecap[tid] : 1024;
-                                int64_t *ne = (int64_t *)realloc(edges[tid], (size_t)nc * 2 * sizeof(int64_t));
-                                if (!ne) {
-                                    failed = 1;
-                                    continue;
-                                }
-                                edges[tid] = ne;
-                                ecap[tid] = nc;
-                            }
-                            edges[tid][2 * ecount[tid]] = pairs[2 * sa->first + 1];
-                            edges[tid][2 * ecount[tid] + 1] = pairs[2 * sb->first + 1];
-                            ecount[tid]++;
-                        }
+                        if ((la || lb) && edge_push(&E[tid], pt[cfirst[ca]], pt[cfirst[cb]], la))
+                            failed = 1;
                     }
+                }
+            }
         }
+        free(nb_first);
+        free(nb_last);
+        free(nb_row);
     }
-    for (int t = 0; t < nth; ++t)
-        free(seenbuf[t]);
-    free(seenbuf);
     for (int t = 0; t < nth; ++t) {
-        for (int64_t e = 0; e < ecount[t]; ++e)
-            uf_union(p, edges[t][2 * e], edges[t][2 * e + 1]);
-        free(edges[t]);
+        for (int64_t e = 0; e < E[t].n; ++e) {
+            const int64_t a = E[t].e[3 * e], b = E[t].e[3 * e + 1];
+            if (E[t].e[3 * e + 2])
+                uf_union(p, a, b);
+            if (q)
+                uf_union(q, a, b);
+        }
+        free(E[t].e);
     }
-    free(edges);
-    free(ecount);
-    free(ecap);
-    for (int64_t i = 0; i < n; ++i)
-        labels[i] = (int32_t)uf_find(p, i);
-    free(pairs);
-    free(tab);
-    free(cells);
-    free(p);
+    free(E);
+    for (int64_t i = 0; i < n; ++i) {
+        labels_a[i] = (int32_t)uf_find(p, i);
+        if (q) labels_b[i] = (int32_t)uf_find(q, i);
+    }
+    free(key); free(pt); free(p); free(q); free(cfirst); free(ckey); free(rcell); free(rows);
     return failed ? -2 : 0;
+}
+
+int oracle_fof_cells(const float *xyz, int64_t n, double b, double b2, double L,
+                     int32_t *labels, int nthreads)
+{
+    (void)b;
+    return oracle_fof_cells2(xyz, n, b2, b2, L, labels, NULL, nthreads);
 }

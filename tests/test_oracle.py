@@ -333,6 +333,12 @@ def test_fof_cells_equals_brute(L, gen):
         assert np.array_equal(oracle.fof_cells(x, b, L), oracle.fof_brute(x, b, L))
     # a large linking length relative to the box (many cells per neighbourhood)
     assert np.array_equal(oracle.fof_cells(x[:500], 0.3, L), oracle.fof_brute(x[:500], 0.3, L))
+    # the strict/loose bracket computed in one pass equals two all-pairs runs
+    b = 0.5 * workloads.mean_spacing(n)
+    s_c, l_c = oracle.fof_bracket(x, b, L, rel=0.05, cells=True)
+    s_b, l_b = oracle.fof_bracket(x, b, L, rel=0.05, cells=False)
+    assert np.array_equal(s_c, s_b) and np.array_equal(l_c, l_b)
+    assert not np.array_equal(s_b, l_b)  # the two thresholds differ on this set
 
 
 # ------------------------------------------------------------------ comparison rules
