@@ -46,7 +46,9 @@ typedef enum jzt_error {
     JZT_ERR_WORKSPACE = -4,    /* ws_bytes below jzt_workspace_bytes() */
     JZT_ERR_CAPACITY = -5,     /* device: node or interaction-list capacity exceeded */
     JZT_ERR_INPUT = -6,        /* device: NaN/Inf coordinate, or outside [0,L) when periodic */
-    JZT_ERR_TIMEOUT = -7       /* device: a bounded wait or CAS retry loop gave up */
+    JZT_ERR_TIMEOUT = -7,      /* device: a bounded wait or CAS retry loop gave up */
+    JZT_ERR_INTERNAL = -8      /* device: an internal consistency check failed (a bug; no
+                                  out-of-range access was made) */
 } jzt_error;
 
 /* Tree and walk parameters; a zero field takes the default shown. */

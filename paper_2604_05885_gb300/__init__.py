@@ -33,8 +33,9 @@ JZT_ERR_WORKSPACE = -4
 JZT_ERR_CAPACITY = -5
 JZT_ERR_INPUT = -6
 JZT_ERR_TIMEOUT = -7
+JZT_ERR_INTERNAL = -8
 _NAMES = {0: "ok", -1: "invalid", -2: "unsupported", -3: "cuda", -4: "workspace",
-          -5: "capacity", -6: "input", -7: "timeout"}
+          -5: "capacity", -6: "input", -7: "timeout", -8: "internal"}
 
 # Every entry point declared in include/jzt.h.
 SYMBOLS = ("jzt_workspace_bytes", "jzt_build", "jzt_tree_knn", "jzt_tree_fof", "jzt_knn", "jzt_fof",

@@ -295,9 +295,9 @@ int jzt_status(const void* d_ws, void* stream, jzt_status_info* info) {
   }
   if (m.status != 0) {
     static const char* names[] = {"ok", "invalid", "unsupported", "cuda", "workspace",
-                                  "capacity", "input", "timeout"};
+                                  "capacity", "input", "timeout", "internal"};
     int c = -m.status;
-    g_err = std::string("device status: ") + (c >= 0 && c < 8 ? names[c] : "?") +
+    g_err = std::string("device status: ") + (c >= 0 && c < 9 ? names[c] : "?") +
             " (stage " + std::to_string(m.detail) + ")";
   }
   return m.status;

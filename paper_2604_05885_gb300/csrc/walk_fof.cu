@@ -127,8 +127,13 @@ __global__ void __launch_bounds__(32 * kFofWarps) k_n2n_fof(
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int nbuf = 0;
   bool union_fail = false;
+  const int64_t npar = m->n_nodes[par_plane];
   for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < n_in; t += nw) {
     const int2 pr = arena[in_off + t];
+    if ((uint64_t)(uint32_t)pr.x >= (uint64_t)npar || (uint64_t)(uint32_t)pr.y >= (uint64_t)npar) {
+      if (lane == 0) set_error(m, JZT_ERR_INTERNAL, kStageFof);  // consistency guard
+      continue;
+    }
     const int a0 = spl_par[pr.x], a1 = spl_par[pr.x + 1];
     const int b0 = spl_par[pr.y], b1 = spl_par[pr.y + 1];
     const int Ca = a1 - a0, Cb = b1 - b0;
@@ -241,8 +246,13 @@ __global__ void __launch_bounds__(128) k_l2l_fof(const float4* __restrict__ pts,
   const float halfL = 0.5f * L;
   bool union_fail = false;
   unsigned long long pairs = 0;
+  const int64_t nl = m->n_nodes[0];
   for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < np; t += nw) {
     const int2 pr = arena[off + t];
+    if ((uint64_t)(uint32_t)pr.x >= (uint64_t)nl || (uint64_t)(uint32_t)pr.y >= (uint64_t)nl) {
+      if (lane == 0) set_error(m, JZT_ERR_INTERNAL, kStageFof);  // consistency guard
+      continue;
+    }
     const NodeRec A = leaves[pr.x], B = leaves[pr.y];
     const bool self = pr.x == pr.y;
     pairs += self ? (unsigned long long)A.count * (A.count - 1) / 2

@@ -282,7 +282,12 @@ __global__ void __launch_bounds__(32 * kN2NWarps) k_n2n_knn(const int32_t* __res
     const bool have_par = par_nodes != nullptr;
     if (have_par) pb = par_nodes[P];
     auto load_meta = [&](uint32_t e, float& r2, int& s0, int& cnt, int& code) {
-      const IEntry en = arena[e_off + e];
+      IEntry en = arena[e_off + e];
+      if ((uint64_t)(uint32_t)en.src >= (uint64_t)npar) {  // consistency guard
+        set_error(m, JZT_ERR_INTERNAL, kStageWalk);
+        en.src = 0;
+        en.r2low = INFINITY;
+      }
       r2 = en.r2low;
       s0 = spl_par[en.src];
       cnt = spl_par[en.src + 1] - s0;
@@ -791,6 +796,11 @@ __global__ void __launch_bounds__(32 * kL2LWarps) k_l2l_knn(const float4* __rest
       NodeRec sr;
       if ((uint32_t)lane < nb) {
         en = list[b0 + lane];
+        if ((uint64_t)(uint32_t)en.src >= (uint64_t)nl) {  // consistency guard
+          set_error(m, JZT_ERR_INTERNAL, kStageLeaf);
+          en.src = 0;
+          en.r2low = INFINITY;
+        }
         sr = leaves[en.src];
       } else {
         sr.count = 0;
