@@ -122,6 +122,7 @@ int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* L
   for (int p = 0; p < L.n_planes; ++p) L.nsz[p] = take(4 * (size_t)(L.cap_nodes[p] + 1));
   for (int p = 0; p < L.n_planes; ++p) L.nodes[p] = take(sizeof(NodeRec) * (size_t)L.cap_nodes[p]);
   for (int p = 0; p <= L.n_planes; ++p) L.ilo[p] = take(8 * (size_t)L.cap_nodes[p]);
+  for (int p = 0; p < L.n_planes; ++p) L.rint[p] = take(4 * (size_t)L.cap_nodes[p]);
   for (int p = 0; p < L.n_planes; ++p) L.ig[p] = take(4 * (size_t)L.cap_nodes[p]);
   for (int p = 0; p < L.n_planes; ++p) L.lk[p] = take((size_t)L.cap_nodes[p]);
   L.ig_pt = take(4 * (size_t)n);

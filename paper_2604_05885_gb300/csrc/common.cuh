@@ -81,6 +81,7 @@ struct Layout {
   size_t nodes[kMaxPlanes];     // NodeRec per node
   size_t ilo[kMaxPlanes + 1];   // uint2 (offset, count) per receiving node; [n_planes] = supers
   size_t arena;                 // IEntry[cap_ilist]
+  size_t rint[kMaxPlanes];      // kNN: float squared internal radius bound per node
   size_t ig[kMaxPlanes];        // FoF: int32 group pointer per node
   size_t lk[kMaxPlanes];        // FoF: uint8 linked flag per node
   size_t ig_pt;                 // FoF: int32 group pointer per sorted point

@@ -253,6 +253,50 @@ __device__ __forceinline__ float centre_d2(const NodeRec& a, const NodeRec& b, i
   return s;
 }
 
+// Internal radius bound of every node of plane p >= 1, bottom-up: for each child
+// c, the smallest radius whose d_up-ball holds k points of its siblings (itself
+// included; RadiusOfCount over the parent's own children, Alg. 3's heap) and,
+// when c has children, c's own bound; the node's bound is the largest over its
+// children.  Every point of the node has its k nearest neighbours within it, so
+// it caps the node's R_max in the walk.  One warp per node.
+template <int NR, bool PER>
+__global__ void __launch_bounds__(128) k_internal_bounds(const int32_t* __restrict__ spl,
+                                                         const NodeRec* __restrict__ child,
+                                                         const float* __restrict__ rint_child,
+                                                         float* __restrict__ rint, int plane, int k,
+                                                         float L, const Meta* m) {
+  if (warp_failed(m)) return;
+  const int64_t nn = m->n_nodes[plane];
+  const int lane = lane_id();
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t P = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; P < nn; P += nw) {
+    const int s0 = spl[P], s1 = spl[P + 1];
+    float worst = 0.0f;
+    for (int c0 = s0; c0 < s1; c0 += 32) {
+      const int c = c0 + lane;
+      const bool act = c < s1;
+      NodeRec me;
+      if (act) me = child[c];
+      else {
+        me.lo[0] = me.lo[1] = me.lo[2] = 0.0f;
+        me.hi[0] = me.hi[1] = me.hi[2] = 0.0f;
+      }
+      const float own = (act && rint_child != nullptr) ? rint_child[c] : INFINITY;
+      RHeap<NR> H;
+      H.init();
+      for (int sb = s0; sb < s1; ++sb) {
+        const NodeRec o = child[sb];
+        const float u2 = box_dup2<PER>(me.lo, me.hi, o.lo, o.hi, L);
+        if (act && u2 < fminf(H.rad, own)) H.insert(u2, o.count, k);
+      }
+      if (act) worst = fmaxf(worst, fminf(H.rad, own));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(kFull, worst, o));
+    if (lane == 0) rint[P] = worst;
+  }
+}
+
 // One warp per receiving parent; G lanes per child split the candidates (the
 // children of the parent's source parents).  The list metadata (first child,
 // child count, r_low^2 and image code of each source) is gathered once per
@@ -262,6 +306,7 @@ __global__ void __launch_bounds__(32 * kN2NWarps) k_n2n_knn(const int32_t* __res
                                                             const uint2* __restrict__ ilo_par,
                                                             const NodeRec* __restrict__ par_nodes,
                                                             const NodeRec* __restrict__ nodes,
+                                                            const float* __restrict__ rint,
                                                             uint2* __restrict__ ilo_out, IEntry* arena,
                                                             int par_plane, int k, float L,
                                                             int64_t cap_ilist, int64_t ws_total,
@@ -340,14 +385,16 @@ __global__ void __launch_bounds__(32 * kN2NWarps) k_n2n_knn(const int32_t* __res
         me.count = 0;
         me.first = 0;
       }
-      // ---- FindRmax (Alg. 3)
+      // ---- FindRmax (Alg. 3), capped by the node's internal bound (no candidate
+      // at or beyond the cap can lower the result below it)
+      const float cap2 = (rint != nullptr && act) ? rint[cl] : INFINITY;
       RHeap<NR> H;
       H.init();
       for (uint32_t e = 0; e < e_cnt; ++e) {
         float r2;
         int s0, cnt, code;
         entry(e, r2, s0, cnt, code);
-        const bool need = act && r2 < H.rad;
+        const bool need = act && r2 < fminf(H.rad, cap2);
         if (!__any_sync(kFull, need)) {
           if (sorted) break;
           continue;
@@ -356,7 +403,7 @@ __global__ void __launch_bounds__(32 * kN2NWarps) k_n2n_knn(const int32_t* __res
           if (need) {
             const NodeRec o = nodes[s0 + j];
             const float u2 = box_bound2<PER, true>(me, o, code, L);
-            if (u2 < H.rad) H.insert(u2, o.count, k);
+            if (u2 < fminf(H.rad, cap2)) H.insert(u2, o.count, k);
           }
         }
       }
@@ -375,7 +422,7 @@ __global__ void __launch_bounds__(32 * kN2NWarps) k_n2n_knn(const int32_t* __res
           if (act && cc > 0 && rr < H.rad) H.insert(rr, cc, k);
         }
       }
-      const float R2 = __shfl_sync(kFull, H.rad, lane & ~(G - 1));
+      const float R2 = fminf(__shfl_sync(kFull, H.rad, lane & ~(G - 1)), cap2);
       // ---- Count
       uint32_t cnt_out = 0;
       for (uint32_t e = 0; e < e_cnt; ++e) {
@@ -955,8 +1002,9 @@ void n2n_knn_plane(const Layout& L, char* ws, int p, int k, float pl, cudaStream
   Meta* m = at<Meta>(ws, L.meta);
   const int sms = 152;
   const NodeRec* par_nodes = (p + 1 < L.n_planes) ? at<NodeRec>(ws, L.nodes[p + 1]) : nullptr;
+  const float* rint = p >= 1 ? at<float>(ws, L.rint[p]) : nullptr;
   k_n2n_knn<NR, PER><<<grid_for(L.cap_nodes[p + 1] * 32, 32 * kN2NWarps, sms * 16), 32 * kN2NWarps, 0, s>>>(
-      at<int32_t>(ws, L.spl[p + 1]), at<uint2>(ws, L.ilo[p + 1]), par_nodes, at<NodeRec>(ws, L.nodes[p]),
+      at<int32_t>(ws, L.spl[p + 1]), at<uint2>(ws, L.ilo[p + 1]), par_nodes, at<NodeRec>(ws, L.nodes[p]), rint,
       at<uint2>(ws, L.ilo[p]), at<IEntry>(ws, L.arena), p + 1, k, pl, L.cap_ilist,
       (int64_t)L.total, m); note_launch();
 }
@@ -982,6 +1030,12 @@ void knn_all(const Layout& L, char* ws, float pl, int k, int order, int32_t* idx
   launch_super_level(L, ws, s);
   k_dense_ilist<<<grid_for(L.cap_nodes[P], 128, sms * 4), 128, 0, s>>>(
       m, at<uint2>(ws, L.ilo[P]), at<IEntry>(ws, L.arena), P, 0, L.cap_ilist, m); note_launch();
+  for (int p = 1; p < P; ++p) {
+    const float* rc = p >= 2 ? at<float>(ws, L.rint[p - 1]) : nullptr;
+    k_internal_bounds<8, PER><<<grid_for(L.cap_nodes[p] * 32, 128, sms * 16), 128, 0, s>>>(
+        at<int32_t>(ws, L.spl[p]), at<NodeRec>(ws, L.nodes[p - 1]), rc, at<float>(ws, L.rint[p]), p, k, pl,
+        m); note_launch();
+  }
   prof_end(kPhKnnTop, s);
   for (int p = P - 1; p >= 0; --p) {
     prof_begin(kPhKnnN2N, s);
