@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--cpu-side", type=float, default=0.375,
                     help="side of the sub-cube of the workload timed on the CPU")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--nmax0", type=int, default=0, help="leaf capacity (0 = library default)")
     ap.add_argument("--cache", default=os.path.join(tempfile.gettempdir(), "jzt_bench_cache"))
     return ap.parse_args()
 
@@ -199,14 +200,15 @@ def main():
     dev = torch.device("cuda", local)
     x = workload(n_side, a.cache)
     x_dev = torch.from_numpy(x).to(dev)
-    ws = jzt.alloc_workspace(n, k, None, dev)
+    params = {"nmax0": a.nmax0} if a.nmax0 else None
+    ws = jzt.alloc_workspace(n, k, params, dev)
     idx = torch.empty((n, k), dtype=torch.int32, device=dev)
     d2 = torch.empty((n, k), dtype=torch.float32, device=dev)
     lab = torch.empty(n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(xd):
-        tree = jzt.build(xd, periodic_L=L, workspace=ws)
+        tree = jzt.build(xd, periodic_L=L, workspace=ws, params=params)
         tree.knn(k, out=(idx, d2))
         tree.fof(b, out=lab)
         return tree

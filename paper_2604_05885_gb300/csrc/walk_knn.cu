@@ -624,10 +624,19 @@ __device__ __forceinline__ float point_box_d2(float4 q, const NodeRec& b, float 
   return s * kLowSlack;
 }
 
-constexpr int kQCap = 8;       // queued candidates per lane before a merge
+#ifndef JZT_L2L_QCAP
+#define JZT_L2L_QCAP 8
+#endif
+#ifndef JZT_L2L_STAGES
+#define JZT_L2L_STAGES 4
+#endif
+#ifndef JZT_L2L_MINBLOCKS
+#define JZT_L2L_MINBLOCKS(kmax) 1
+#endif
+constexpr int kQCap = JZT_L2L_QCAP;      // queued candidates per lane before a merge
 constexpr int kL2LWarps = 4;
-constexpr int kStages = 4;     // source leaves in flight per warp
-constexpr int kUnroll = 4;     // source points per vote
+constexpr int kStages = JZT_L2L_STAGES;  // source leaves in flight per warp
+constexpr int kUnroll = 4;               // source points per vote
 
 // Candidates are packed as (float32 bits of d2) << 32 | (original index + 1):
 // for d2 >= 0 the unsigned order of the key is the order by (d2, index), and 0
@@ -789,7 +798,7 @@ __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt
 // one entry per lane.  Each query lane keeps its k best (d2, index) keys in a
 // sorted register list (RegTopK); its last key is the running k-th distance.
 template <int KMAX, bool PER>
-__global__ void __launch_bounds__(32 * kL2LWarps) k_l2l_knn(const float4* __restrict__ pts,
+__global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l_knn(const float4* __restrict__ pts,
                                                            const NodeRec* __restrict__ leaves,
                                                            const uint2* __restrict__ ilo,
                                                            const IEntry* __restrict__ arena, int k,
