@@ -91,6 +91,7 @@ int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* L
   double nmax = P.nmax0;
   for (int p = 0; p < L.n_planes; ++p) {
     double est = std::ceil((double)P.fac_nodes * (double)n / (nmax / 2.0));
+    if (p == 0) est = std::max(est, 4096.0);  // small sets: room for mostly tiny leaves
     if (p > 0) est = 4.0 * est + 256.0;
     int64_t cap = (int64_t)std::min<double>(est, (double)n);
     if (p > 0) cap = std::min<int64_t>(cap, L.cap_nodes[p - 1]);

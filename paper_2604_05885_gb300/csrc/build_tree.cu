@@ -121,7 +121,17 @@ __global__ void k_init_meta(Meta* m, int n_planes) {
     m->bbox_enc[t] = 0xffffffffu;
     m->bbox_enc[3 + t] = 0u;
   }
-  if (t < kMaxPlanes + 1) m->n_nodes[t] = 0;
+  if (t < kMaxPlanes + 1) {
+    m->n_nodes[t] = 0;
+    m->pair_off[t] = 0;
+    m->pair_cnt[t] = 0;
+  }
+  if (t < kMaxPlanes) m->knn_plane_entries[t] = 0;
+  if (t < 8) m->knn_stats[t] = 0;
+  if (t == 0) {
+    m->knn_pairs = 0;
+    m->fof_pairs = 0;
+  }
   if (t < 32) m->tile_ctr[t] = 0;
   uint32_t* h = &m->radix_hist[0][0];
   for (int i = t; i < kRadixPasses * kRadixBins; i += blockDim.x) h[i] = 0;

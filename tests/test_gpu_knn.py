@@ -70,10 +70,11 @@ def test_duplicates_and_degenerate_geometry():
     knn_parity(tree, line, 8, 0.0)
 
 
-@pytest.mark.parametrize("n,k", [(1, 1), (2, 2), (3, 1), (32, 32), (33, 32), (100, 7)])
-def test_tiny_sets(n, k):
+@pytest.mark.parametrize("n,k", [(1, 1), (2, 2), (3, 1), (32, 32), (33, 32), (52, 1), (100, 7)])
+@pytest.mark.parametrize("gen", ["uniform", "clustered"])
+def test_tiny_sets(n, k, gen):
     import paper_2604_05885_gb300 as jzt
-    x = workloads.uniform(n, 100 + n)
+    x = workloads.uniform(n, 100 + n) if gen == "uniform" else workloads.clustered(n, 7000 + n, n_blobs=2)
     for L in (0.0, 1.0):
         tree = jzt.build(to_dev(x), periodic_L=L)
         knn_parity(tree, x, k, L)
