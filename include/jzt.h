@@ -151,6 +151,40 @@ int jzt_tree_plane(const jzt_tree *t, int p, int64_t cap, int64_t *n_nodes,
 
 void jzt_tree_free(jzt_tree *t);
 
+/* ---- Batched jobs (no counterpart in the paper: a system pattern on top of the
+ * method).  Each job is an independent point set with its own operation. */
+enum { JZT_OP_KNN = 0, JZT_OP_FOF = 1 };
+
+typedef struct jzt_job {
+    const float *d_xyz;   /* N x 3 float32 points (device) */
+    int64_t n;            /* 1 <= N < 2^30 */
+    float periodic_L;     /* > 0: periodic box [0,L)^3 */
+    int32_t op;           /* JZT_OP_KNN or JZT_OP_FOF */
+    int32_t k;            /* kNN: neighbours per point, 1..min(32, N) */
+    float b;              /* FoF: linking length */
+    int32_t lane;         /* lane (0 <= lane < n_lanes) that runs the job */
+    int32_t pad;
+    int32_t *d_idx;       /* kNN output, N x k (input order), as jzt_tree_knn */
+    float *d_dist2;       /* kNN output, N x k */
+    int32_t *d_labels;    /* FoF output, N, as jzt_tree_fof */
+} jzt_job;
+
+/* Runs n_jobs jobs: the work of each job is exactly that of jzt_knn / jzt_fof
+ * (same results).  Job j runs on lane jobs[j].lane, i.e. on lane_streams[lane]
+ * with workspace d_lane_ws[lane] of lane_ws_bytes[lane] bytes (at least
+ * jzt_workspace_bytes of every job on that lane, for that job's k); jobs on one
+ * lane run in array order and reuse its workspace, lanes run concurrently.  The
+ * lanes fork from `stream` and join back into it with events, so the batch is
+ * ordered like one operation on `stream` and can be captured into a CUDA graph
+ * (capture `stream`; the lane streams join the capture through the events).
+ * d_job_status (device, n_jobs int32) receives each job's device status code
+ * (JZT_OK or a device-side jzt_error) when the job ends.  All arguments are
+ * validated before anything is enqueued (JZT_ERR_INVALID / _UNSUPPORTED /
+ * _WORKSPACE with a message naming the job). */
+int jzt_batch_run(const jzt_job *jobs, int n_jobs, const jzt_params *p,
+                  void *const *d_lane_ws, const size_t *lane_ws_bytes,
+                  void *const *lane_streams, int n_lanes, void *stream, int32_t *d_job_status);
+
 /* Allocation-free form of jzt_knn (the paper has no counterpart: this is for
  * callers that may not allocate device memory, e.g. inside a framework that owns
  * all device allocations, or during stream capture).  Same results as jzt_knn

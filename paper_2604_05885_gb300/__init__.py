@@ -41,7 +41,9 @@ _NAMES = {0: "ok", -1: "invalid", -2: "unsupported", -3: "cuda", -4: "workspace"
 SYMBOLS = ("jzt_workspace_bytes", "jzt_build", "jzt_tree_knn", "jzt_tree_fof", "jzt_knn", "jzt_fof",
            "jzt_status", "jzt_tree_arrays", "jzt_tree_plane", "jzt_tree_free", "jzt_last_error",
            "jzt_version", "jzt_profile_enable", "jzt_profile_read", "jzt_profile_phase_name",
-           "jzt_knn_noalloc")
+           "jzt_knn_noalloc", "jzt_batch_run")
+JZT_OP_KNN = 0
+JZT_OP_FOF = 1
 
 
 class JztError(RuntimeError):
@@ -56,6 +58,14 @@ class Params(ctypes.Structure):
                 ("n_target", ctypes.c_int32), ("ngr", ctypes.c_int32),
                 ("alloc_fac_nodes", ctypes.c_float), ("alloc_fac_ilist", ctypes.c_float),
                 ("heap_size", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class Job(ctypes.Structure):
+    """Mirror of jzt_job."""
+    _fields_ = [("d_xyz", ctypes.c_void_p), ("n", ctypes.c_int64), ("periodic_L", ctypes.c_float),
+                ("op", ctypes.c_int32), ("k", ctypes.c_int32), ("b", ctypes.c_float), ("lane", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("d_idx", ctypes.c_void_p), ("d_dist2", ctypes.c_void_p),
+                ("d_labels", ctypes.c_void_p)]
 
 
 class StatusInfo(ctypes.Structure):
@@ -91,6 +101,9 @@ def _load():
     lib.jzt_profile_phase_name.restype = ctypes.c_char_p
     lib.jzt_knn_noalloc.argtypes = [vp, i64, ctypes.c_int, f32, vp, vp, vp, ctypes.POINTER(StatusInfo)]
     lib.jzt_knn_noalloc.restype = ctypes.c_int
+    lib.jzt_batch_run.argtypes = [ctypes.POINTER(Job), ctypes.c_int, ctypes.POINTER(Params),
+                                  ctypes.POINTER(vp), ctypes.POINTER(sz), ctypes.POINTER(vp), ctypes.c_int, vp, vp]
+    lib.jzt_batch_run.restype = ctypes.c_int
     lib.jzt_tree_free.argtypes = [vp]
     lib.jzt_tree_free.restype = None
     lib.jzt_last_error.restype = ctypes.c_char_p
@@ -289,3 +302,89 @@ def fof(xyz: torch.Tensor, b: float, periodic_L: float = 0.0, workspace=None, st
     if check:
         status(ws, stream, raise_on_error=True)
     return lab
+
+
+class Batch:
+    """Independent kNN / FoF jobs run on concurrent lanes through jzt_batch_run,
+    optionally captured once into a CUDA graph and replayed.
+
+    sets: list of dicts with keys ``points`` (contiguous CUDA float32 tensor N x 3),
+    ``op`` ('knn' or 'fof'), ``k`` (kNN), ``b`` (FoF), ``periodic_L`` (default 0).
+    Jobs are spread over ``n_lanes`` lanes by longest-processing-time order (each
+    to the least loaded lane); every lane gets one workspace sized for its largest
+    job.  Outputs: ``outputs[j]`` is (idx, dist2) for kNN jobs and labels for FoF.
+    """
+
+    def __init__(self, sets, n_lanes: int = 8, params=None, graph: bool = True, device=None):
+        if not sets:
+            raise ValueError("empty batch")
+        dev = torch.device(device) if device is not None else sets[0]["points"].device
+        self.sets = sets
+        self.params = params
+        nj = len(sets)
+        n_lanes = max(1, min(int(n_lanes), nj))
+        self.n_lanes = n_lanes
+        sizes = [int(s["points"].shape[0]) for s in sets]
+        order = sorted(range(nj), key=lambda j: -sizes[j])
+        load = [0] * n_lanes
+        lane_of = [0] * nj
+        for j in order:
+            lane = min(range(n_lanes), key=lambda q: load[q])
+            lane_of[j] = lane
+            load[lane] += sizes[j]
+        need = [0] * n_lanes
+        for j, st in enumerate(sets):
+            _check_xyz(st["points"])
+            k = int(st.get("k", 0)) if st["op"] == "knn" else 0
+            need[lane_of[j]] = max(need[lane_of[j]], workspace_bytes(sizes[j], min(k, sizes[j]), params))
+        self.ws = [torch.empty(need[q], dtype=torch.uint8, device=dev) for q in range(n_lanes)]
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(n_lanes)]
+        self.job_status = torch.zeros(nj, dtype=torch.int32, device=dev)
+        self.outputs = []
+        self.jobs = (Job * nj)()
+        for j, st in enumerate(sets):
+            J = self.jobs[j]
+            J.d_xyz = st["points"].data_ptr()
+            J.n = sizes[j]
+            J.periodic_L = float(st.get("periodic_L", 0.0))
+            J.lane = lane_of[j]
+            if st["op"] == "knn":
+                k = int(st["k"])
+                idx = torch.empty((sizes[j], k), dtype=torch.int32, device=dev)
+                d2 = torch.empty((sizes[j], k), dtype=torch.float32, device=dev)
+                J.op, J.k, J.d_idx, J.d_dist2 = JZT_OP_KNN, k, idx.data_ptr(), d2.data_ptr()
+                self.outputs.append((idx, d2))
+            elif st["op"] == "fof":
+                lab = torch.empty(sizes[j], dtype=torch.int32, device=dev)
+                J.op, J.b, J.d_labels = JZT_OP_FOF, float(st["b"]), lab.data_ptr()
+                self.outputs.append(lab)
+            else:
+                raise ValueError(f"job {j}: op must be 'knn' or 'fof'")
+        self._ws_ptrs = (ctypes.c_void_p * n_lanes)(*[w.data_ptr() for w in self.ws])
+        self._ws_bytes = (ctypes.c_size_t * n_lanes)(*[w.numel() for w in self.ws])
+        self._streams = (ctypes.c_void_p * n_lanes)(*[st.cuda_stream for st in self.streams])
+        self.graph = None
+        self._launch(torch.cuda.current_stream(dev))  # eager run (also warms up the kernels)
+        if graph:
+            torch.cuda.synchronize(dev)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, capture_error_mode="relaxed"):
+                self._launch(torch.cuda.current_stream(dev))
+            self.graph = g
+
+    def _launch(self, stream):
+        _check(lib.jzt_batch_run(self.jobs, len(self.sets), _params(self.params), self._ws_ptrs,
+                                 self._ws_bytes, self._streams, self.n_lanes,
+                                 ctypes.c_void_p(stream.cuda_stream),
+                                 ctypes.c_void_p(self.job_status.data_ptr())))
+
+    def run(self):
+        """Enqueue the whole batch on the current stream (graph replay when captured)."""
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._launch(torch.cuda.current_stream())
+
+    def statuses(self):
+        """Per-job device status codes (synchronises)."""
+        return self.job_status.cpu().tolist()
