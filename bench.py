@@ -47,11 +47,20 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-side", type=float, default=0.25,
                     help="side of the sub-cube timed per step by --impl reference")
-    ap.add_argument("--cpu-side", type=float, default=0.375,
+    ap.add_argument("--cpu-side", type=float, default=0.75,
                     help="side of the sub-cube of the workload timed on the CPU")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--nmax0", type=int, default=0, help="leaf capacity (0 = library default)")
     ap.add_argument("--cache", default=os.path.join(tempfile.gettempdir(), "jzt_bench_cache"))
+    ap.add_argument("--batch-sets", type=int, default=512, help="batched sets (0 = skip the batched run)")
+    ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1000, help="served requests (0 = skip serving)")
+    ap.add_argument("--serve-lanes", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="arrival rate as a fraction of the one-call server's measured capacity")
+    ap.add_argument("--serve-sweep", default="", help="comma-separated extra loads to run both servers at")
     return ap.parse_args()
 
 
@@ -142,6 +151,156 @@ def cpu_baseline(x, n_side, k, b, side, threads=0):
             "sample": f"{n} points of the sub-cube [0,{side})^3 of the {n_side}^3 Zel'dovich set, "
                       f"open box; cell-list kNN k={k} ({t1 - t0:.1f} s) + cell-list FoF ({t2 - t1:.1f} s)",
             "seconds": t2 - t0}
+
+
+def batched_run(a, dev, log):
+    """512 independent clustered sets (sizes log-uniform 1e3..2e6, per-set kNN k
+    in {8,16,32} or FoF b in {0.15,0.2,0.25} x spacing), run as one Batch replayed
+    from a CUDA graph with autotuned lanes and tree parameters, against one
+    jzt_knn / jzt_fof call per set on one stream; outputs compared bitwise."""
+    import torch
+
+    import paper_2604_05885_gb300 as jzt
+    import workloads
+    from paper_2604_05885_gb300 import autotune
+
+    t = time.perf_counter()
+    host = workloads.batched_sets(a.batch_sets, 4, workers=min(16, os.cpu_count() or 1))
+    gen_s = time.perf_counter() - t
+    sets = [dict(points=torch.from_numpy(h["points"]).to(dev), op=h["op"], k=h["k"], b=h["b"],
+                 periodic_L=h["periodic_L"]) for h in host]
+    del host
+    total = sum(int(st["points"].shape[0]) for st in sets)
+    t = time.perf_counter()
+    if a.no_autotune:
+        n_lanes, params = 8, {}
+    else:
+        n_lanes, params = autotune.tune(sets, cache=os.path.join(a.cache, "autotune.json"), log=log)
+    tune_s = time.perf_counter() - t
+    batch = jzt.Batch(sets, n_lanes=n_lanes, params=params or None, graph=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        for _ in range(max(3, a.warmup)):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    ms_batch = timed(batch.run, a.batch_steps)
+    bad = [j for j, c in enumerate(batch.statuses()) if c != 0]
+    # one call per set on one stream, one workspace sized for the largest set
+    ws = jzt.alloc_workspace(max(int(st["points"].shape[0]) for st in sets), 32, None, dev)
+    outs = []
+    for st in sets:
+        n = int(st["points"].shape[0])
+        if st["op"] == "knn":
+            outs.append((torch.empty((n, st["k"]), dtype=torch.int32, device=dev),
+                         torch.empty((n, st["k"]), dtype=torch.float32, device=dev)))
+        else:
+            outs.append(torch.empty(n, dtype=torch.int32, device=dev))
+
+    def one_call_per_set():
+        for st, out in zip(sets, outs):
+            if st["op"] == "knn":
+                jzt.knn(st["points"], st["k"], st["periodic_L"], workspace=ws, check=False, out=out)
+            else:
+                jzt.fof(st["points"], st["b"], st["periodic_L"], workspace=ws, check=False, out=out)
+
+    ms_plain = timed(one_call_per_set, a.batch_steps)
+    jzt.status(ws, raise_on_error=True)
+    same = True
+    for st, ob, op in zip(sets, batch.outputs, outs):
+        if st["op"] == "knn":
+            same &= bool(torch.equal(ob[0], op[0]) and torch.equal(ob[1], op[1]))
+        else:
+            same &= bool(torch.equal(ob, op))
+    n_knn = sum(1 for st in sets if st["op"] == "knn")
+    res = {"workload": f"{len(sets)} clustered sets, sizes log-uniform 1e3..2e6, seed 4",
+           "points": total, "knn_sets": n_knn, "fof_sets": len(sets) - n_knn,
+           "lanes": batch.n_lanes, "params": params or {}, "graph": True,
+           "value": total / (ms_batch / 1000.0), "unit": "particles/s", "ms_per_batch": ms_batch,
+           "one_call_per_set": {"value": total / (ms_plain / 1000.0), "ms_per_batch": ms_plain},
+           "speedup": ms_plain / ms_batch, "identical_results": same, "failed_jobs": bad,
+           "steps": a.batch_steps, "autotune_s": tune_s, "generate_s": gen_s}
+    del batch, outs, ws, sets
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+    return res
+
+
+def serving_run(a, dev, log):
+    """Poisson stream of kNN/FoF requests (sizes log-uniform 1e4..2^24, 30 % on an
+    earlier set), served by the continuous-batching Server (lanes, HBM budget,
+    resident trees) and by the one-call-per-request PlainServer, both at the same
+    arrival rate: serve_load x the one-call server's measured capacity."""
+    import torch
+
+    import workloads
+    from paper_2604_05885_gb300.serve import PlainServer, Request, Server, latency_summary
+
+    spec = workloads.serving_stream(a.serve_requests, 5, rate_hz=1.0)
+    seeds = {r["set_id"]: r["seed"] for r in spec}
+
+    def payload(sid, n, stream):
+        return workloads.clustered_device(n, seeds[sid], dev)
+
+    def requests(rate):
+        """The stream at ``rate`` requests/s (rate None: every request at t = 0)."""
+        return [Request(i, r["set_id"], r["n"], r["op"], r["k"], r["b"], 1.0,
+                        0.0 if rate is None else r["t_arrival"] / rate)
+                for i, r in enumerate(spec)]
+
+    max_n = max(r["n"] for r in spec)
+    plain = PlainServer(payload, max_n, device=dev)
+    warm = [Request(i, -1 - i, n, op, k, b, 1.0, 0.0)
+            for i, (n, op, k, b) in enumerate([(20000, "knn", 16, 0.0), (300000, "fof", 0, 0.001),
+                                               (20000, "fof", 0, 0.01), (300000, "knn", 32, 0.0)])]
+    for sd in range(4):
+        seeds[-1 - sd] = 99 + sd
+    plain.run(warm, realtime=False)
+    cap_plain = latency_summary(plain.run(requests(None), realtime=False))
+    rate = a.serve_load * cap_plain["requests_per_s"]
+    log(f"one-call capacity {cap_plain['requests_per_s']:.1f} req/s; arrival rate {rate:.1f} req/s")
+    plain_rt = latency_summary(plain.run(requests(rate), realtime=True))
+    sweep = {}
+    loads = [float(v) for v in a.serve_sweep.split(",") if v.strip()]
+    for ld in loads:
+        sweep[str(ld)] = {"one_call_per_request": latency_summary(
+            plain.run(requests(ld * cap_plain["requests_per_s"]), realtime=True))}
+    del plain
+    torch.cuda.empty_cache()
+    srv = Server(payload, n_lanes=a.serve_lanes, hbm_budget=a.serve_budget_gb * 1e9, device=dev)
+    srv.run(warm, realtime=False)
+    srv.clear()
+    served_rt = latency_summary(srv.run(requests(rate), realtime=True))
+    st_rt = dict(srv.stats)
+    peak_rt = srv.peak_used
+    srv.clear()
+    for ld in loads:
+        sweep[str(ld)]["served"] = latency_summary(srv.run(requests(ld * cap_plain["requests_per_s"]),
+                                                           realtime=True))
+        srv.clear()
+    srv.stats = dict.fromkeys(srv.stats, 0)
+    cap_served = latency_summary(srv.run(requests(None), realtime=False))
+    srv.clear()
+    del srv
+    torch.cuda.empty_cache()
+    ns = sorted(r["n"] for r in spec)
+    return {"workload": f"{len(spec)} requests, Poisson arrivals, sizes log-uniform 1e4..2^24, "
+                        f"30% repeat an earlier set, seed 5",
+            "points": sum(ns), "median_n": ns[len(ns) // 2], "arrival_rate_per_s": rate,
+            "load_vs_one_call_capacity": a.serve_load, "lanes": a.serve_lanes,
+            "hbm_budget_gb": a.serve_budget_gb, "served": served_rt, "served_stats": st_rt,
+            "served_peak_bytes": peak_rt, "one_call_per_request": plain_rt,
+            "capacity": {"served": cap_served, "one_call_per_request": cap_plain},
+            "load_sweep": sweep or None}
 
 
 def dist_setup(gpus):
@@ -330,6 +489,22 @@ def main():
             "knn_l2l_entries_examined": st["knn_stats"][0], "knn_l2l_leaves_scanned": st["knn_stats"][1],
             "knn_l2l_candidates_queued": st["knn_stats"][2], "knn_l2l_heap_insertions": st["knn_stats"][3],
             "p50_p99_latency": None}
+    del ws, idx, d2, lab, x_dev, tree
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+
+    def log(msg):
+        print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+    if a.batch_sets > 0:
+        line["batched"] = batched_run(a, dev, log)
+    if a.serve_requests > 0:
+        sv = serving_run(a, dev, log)
+        line["serving"] = sv
+        line["p50_p99_latency"] = {"p50_ms": sv["served"]["p50_ms"], "p99_ms": sv["served"]["p99_ms"],
+                                   "one_call_p50_ms": sv["one_call_per_request"]["p50_ms"],
+                                   "one_call_p99_ms": sv["one_call_per_request"]["p99_ms"],
+                                   "arrival_rate_per_s": sv["arrival_rate_per_s"]}
     if rank == 0 and not a.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(x, n_side, k, b, a.cpu_side)
     if rank == 0:

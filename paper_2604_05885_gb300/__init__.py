@@ -275,13 +275,16 @@ def build(xyz, periodic_L=0.0, params=None, workspace=None, stream=None, k_max=3
     return Tree(xyz, periodic_L, params, workspace, stream, k_max)
 
 
-def knn(xyz: torch.Tensor, k: int, periodic_L: float = 0.0, workspace=None, stream=None, check=True):
+def knn(xyz: torch.Tensor, k: int, periodic_L: float = 0.0, workspace=None, stream=None, check=True, out=None):
     """One-call exact kNN (jzt_knn); returns (idx [N,k] int32, dist2 [N,k] float32)."""
     _check_xyz(xyz)
     n = xyz.shape[0]
     ws = workspace if workspace is not None else alloc_workspace(n, min(k, n), None, xyz.device)
-    idx = torch.empty((n, k), dtype=torch.int32, device=xyz.device)
-    d2 = torch.empty((n, k), dtype=torch.float32, device=xyz.device)
+    if out is None:
+        idx = torch.empty((n, k), dtype=torch.int32, device=xyz.device)
+        d2 = torch.empty((n, k), dtype=torch.float32, device=xyz.device)
+    else:
+        idx, d2 = out
     _check(lib.jzt_knn(ctypes.c_void_p(xyz.data_ptr()), n, int(k), float(periodic_L),
                        ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(_stream(stream))))
@@ -290,12 +293,12 @@ def knn(xyz: torch.Tensor, k: int, periodic_L: float = 0.0, workspace=None, stre
     return idx, d2
 
 
-def fof(xyz: torch.Tensor, b: float, periodic_L: float = 0.0, workspace=None, stream=None, check=True):
+def fof(xyz: torch.Tensor, b: float, periodic_L: float = 0.0, workspace=None, stream=None, check=True, out=None):
     """One-call FoF (jzt_fof); returns labels [N] int32 (smallest index of each group)."""
     _check_xyz(xyz)
     n = xyz.shape[0]
     ws = workspace if workspace is not None else alloc_workspace(n, 0, None, xyz.device)
-    lab = torch.empty(n, dtype=torch.int32, device=xyz.device)
+    lab = out if out is not None else torch.empty(n, dtype=torch.int32, device=xyz.device)
     _check(lib.jzt_fof(ctypes.c_void_p(xyz.data_ptr()), n, float(b), float(periodic_L),
                        ctypes.c_void_p(lab.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                        ctypes.c_void_p(_stream(stream))))

@@ -160,29 +160,73 @@ def config_zeldovich(n_side: int = 512) -> tuple[Workload, np.ndarray]:
     return w, zeldovich(n_side, 3)
 
 
-def batched_sets(n_sets: int = 512, seed: int = 4, n_lo: float = 1e3, n_hi: float = 2e6,
-                 total_cap: int | None = None):
-    """Independent clustered sets with log-uniform sizes, each with its own op.
-
-    Returns a list of dicts {points, op ('knn'|'fof'), k, b, periodic_L}.
-    Blob count scales with the set size so blob occupancy matches the 2^24 case.
-    """
+def batched_specs(n_sets: int = 512, seed: int = 4, n_lo: float = 1e3, n_hi: float = 2e6,
+                  total_cap: int | None = None):
+    """The per-set draws of ``batched_sets`` without the points: a list of dicts
+    {n, seed, n_blobs, op ('knn'|'fof'), k, b, periodic_L}."""
     rng = np.random.Generator(np.random.PCG64(seed))
     sizes = np.floor(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), n_sets))).astype(np.int64)
     if total_cap is not None:
         while sizes.sum() > total_cap:
             sizes = np.maximum(sizes // 2, 1)
-    jobs = []
-    for s, n in enumerate(sizes):
-        sub_seed = int(rng.integers(0, 2**62))
-        blobs = max(1, int(n) // 4096)
-        pts = clustered(int(n), sub_seed, n_blobs=blobs)
+    specs = []
+    for n in sizes:
+        spec = dict(n=int(n), seed=int(rng.integers(0, 2**62)), n_blobs=max(1, int(n) // 4096), periodic_L=1.0)
         if rng.random() < 0.5:
-            jobs.append(dict(points=pts, op="knn", k=int(rng.choice([8, 16, 32])), b=0.0, periodic_L=1.0))
+            spec.update(op="knn", k=int(rng.choice([8, 16, 32])), b=0.0)
         else:
             fac = float(rng.choice([0.15, 0.2, 0.25]))
-            jobs.append(dict(points=pts, op="fof", k=0, b=fac * mean_spacing(int(n)), periodic_L=1.0))
-    return jobs
+            spec.update(op="fof", k=0, b=fac * mean_spacing(int(n)))
+        specs.append(spec)
+    return specs
+
+
+def _clustered_spec(spec):
+    return clustered(spec["n"], spec["seed"], n_blobs=spec["n_blobs"])
+
+
+def batched_sets(n_sets: int = 512, seed: int = 4, n_lo: float = 1e3, n_hi: float = 2e6,
+                 total_cap: int | None = None, workers: int = 1):
+    """Independent clustered sets with log-uniform sizes, each with its own op.
+
+    Returns a list of dicts {points, op ('knn'|'fof'), k, b, periodic_L}.
+    Blob count scales with the set size so blob occupancy matches the 2^24 case.
+    ``workers`` > 1 draws the sets in that many spawned processes (same points).
+    """
+    specs = batched_specs(n_sets, seed, n_lo, n_hi, total_cap)
+    if workers > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            pts = list(ex.map(_clustered_spec, specs, chunksize=4))
+    else:
+        pts = [_clustered_spec(sp) for sp in specs]
+    return [dict(points=x, op=sp["op"], k=sp["k"], b=sp["b"], periodic_L=sp["periodic_L"])
+            for sp, x in zip(specs, pts)]
+
+
+def clustered_device(n: int, seed: int, device, n_blobs: int | None = None, frac_blob: float = 0.7,
+                     sigma_lo: float = 1e-4, sigma_hi: float = 1e-2):
+    """Device-side draw of a ``clustered``-shaped set (same recipe, torch's Philox
+    generator instead of PCG64, so the points differ from ``clustered``'s): for
+    sets too large or too many to draw on the host.  Deterministic for a given
+    (n, seed, device type); coordinates on the 2**-24 grid in [0, 1), float32."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) % (2**63))
+    nb = max(1, int(n_blobs if n_blobs is not None else n // 4096))
+    centres = torch.rand((nb, 3), generator=g, device=device, dtype=torch.float64)
+    sig = torch.exp(torch.empty(nb, device=device, dtype=torch.float64).uniform_(
+        math.log(sigma_lo), math.log(sigma_hi), generator=g))
+    n_in = int(round(frac_blob * n))
+    u = torch.empty((n, 3), device=device, dtype=torch.float64)
+    blob = torch.randint(0, nb, (n_in,), generator=g, device=device)
+    u[:n_in] = centres[blob] + torch.randn((n_in, 3), generator=g, device=device,
+                                           dtype=torch.float64) * sig[blob, None]
+    u[n_in:] = torch.rand((n - n_in, 3), generator=g, device=device, dtype=torch.float64)
+    perm = torch.randperm(n, generator=g, device=device)
+    q = torch.remainder(torch.floor(u[perm] * SNAP).to(torch.int64), 1 << SNAP_BITS)
+    return (q.to(torch.float64) / SNAP).to(torch.float32).contiguous()
 
 
 def serving_stream(n_req: int = 20000, seed: int = 5, n_lo: float = 1e4, n_hi: float = float(1 << 24),
