@@ -624,8 +624,8 @@ __device__ __forceinline__ float point_box_d2(float4 q, const NodeRec& b, float 
   return s * kLowSlack;
 }
 
-#ifndef JZT_L2L_QCAP
-#define JZT_L2L_QCAP 8
+#ifndef JZT_L2L_QF
+#define JZT_L2L_QF 16
 #endif
 #ifndef JZT_L2L_STAGES
 #define JZT_L2L_STAGES 4
@@ -633,7 +633,7 @@ __device__ __forceinline__ float point_box_d2(float4 q, const NodeRec& b, float 
 #ifndef JZT_L2L_MINBLOCKS
 #define JZT_L2L_MINBLOCKS(kmax) 1
 #endif
-constexpr int kQCap = JZT_L2L_QCAP;      // queued candidates per lane before a merge
+constexpr int kQF = JZT_L2L_QF;          // buffered candidates per lane between threshold updates
 constexpr int kL2LWarps = 4;
 constexpr int kStages = JZT_L2L_STAGES;  // source leaves in flight per warp
 constexpr int kUnroll = 4;               // source points per vote
@@ -646,10 +646,17 @@ __device__ __forceinline__ unsigned long long pack_key(float d2, int idx) {
   return ((unsigned long long)__float_as_uint(d2) << 32) | (uint32_t)(idx + 1);
 }
 
+// Per-warp shared memory: staged source leaves and, per lane, a buffer of
+// candidate (d2 bits, original index) pairs.  The buffer holds KMAX + 32
+// entries, so that after an exact compaction to k entries a full source leaf
+// always fits.
+template <int KMAX>
 struct __align__(16) L2LWarpSmem {
-  float4 pts[kStages][32];              // staged source leaves (<= 32 points each)
+  static constexpr int kCap = KMAX + 32;
+  float4 pts[kStages][32];  // staged source leaves (<= 32 points each)
+  float4 meta[32][3];       // list entries of the current batch (see k_l2l_knn)
   uint64_t bar[kStages];
-  unsigned long long q[kQCap][32];      // per-lane candidate queue
+  uint2 buf[kCap][32];      // buf[slot][lane]
 };
 
 __device__ __forceinline__ void cswap(unsigned long long& a, unsigned long long& b) {
@@ -657,26 +664,28 @@ __device__ __forceinline__ void cswap(unsigned long long& a, unsigned long long&
   a = lo;
   b = hi;
 }
+__device__ __forceinline__ void cswap(float& a, float& b) {
+  const float lo = fminf(a, b), hi = fmaxf(a, b);
+  a = lo;
+  b = hi;
+}
 
-// Sorted top-K of packed keys in registers (ascending; the first K-k slots hold
-// 0 so that the k-th best key is always the last one).  New keys are merged in
-// batches: the batch is sorted with a bitonic network, paired against the list
-// in reverse (which leaves a bitonic sequence holding the K smallest keys of
-// both), and a bitonic merge restores the order.  Branch-free, so lanes with
-// different numbers of new keys do not diverge.
-template <int K>
+// Sorted top-K list in registers (ascending; the first K-k slots hold pads
+// below every real entry so that the k-th best entry is always the last one).
+// New entries are merged in batches: the batch is sorted with a bitonic
+// network, paired against the list in reverse (which leaves a bitonic sequence
+// holding the K smallest of both), and a bitonic merge restores the order.
+// Branch-free, so lanes with different numbers of new entries do not diverge.
+// T is unsigned long long for packed (d2, index) keys, float for distances only.
+template <typename T, int K>
 struct RegTopK {
-  unsigned long long t[K];
-  __device__ __forceinline__ void init(int k) {
+  T t[K];
+  __device__ __forceinline__ void init(int k, T pad, T inf) {
 #pragma unroll
-    for (int e = 0; e < K; ++e) t[e] = e < K - k ? 0ull : kKeyInf;
-  }
-  __device__ __forceinline__ float thr() const {
-    return t[K - 1] == kKeyInf ? INFINITY : __uint_as_float((uint32_t)(t[K - 1] >> 32));
+    for (int e = 0; e < K; ++e) t[e] = e < K - k ? pad : inf;
   }
   template <int B>
-  __device__ __forceinline__ void merge(unsigned long long (&b)[B]) {
-    // sort the batch ascending
+  __device__ __forceinline__ void merge(T (&b)[B]) {
 #pragma unroll
     for (int size = 2; size <= B; size <<= 1)
 #pragma unroll
@@ -689,13 +698,11 @@ struct RegTopK {
             else cswap(b[j], b[i]);
           }
         }
-    // keep the K smallest of both lists: min against the reversed batch
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       const int j = K - 1 - i;
       if (j < B) t[i] = t[i] < b[j] ? t[i] : b[j];
     }
-    // bitonic merge
 #pragma unroll
     for (int stride = K >> 1; stride > 0; stride >>= 1)
 #pragma unroll
@@ -706,17 +713,89 @@ struct RegTopK {
   }
 };
 
-// Merge a lane's queued candidates into its top-k; returns the new k-th distance.
-template <int K>
-__device__ __forceinline__ float flush_queue(unsigned long long (*q)[32], RegTopK<K>& T, int lane,
-                                             int& qn, bool act, uint32_t& n_queued) {
-  unsigned long long b[kQCap];
+// Per-lane candidate state of one query: the buffer (in shared memory) holds
+// nb entries, of which the first nm have been merged into F, the k smallest
+// distances seen so far; F's last entry is the running k-th distance thr.
+// Every source point at or below thr when it is scanned is buffered, so the
+// buffer always holds every point that can still be among the k nearest.
+template <int KMAX>
+struct Cand {
+  RegTopK<float, KMAX> F;
+  int nb, nm;
+  float thr;
+  uint32_t pushed;
+};
+
+// Merge the unmerged buffer entries (at most kQF) into F; returns the new thr.
+template <int KMAX>
+__device__ __forceinline__ void merge_distances(uint2 (*buf)[32], Cand<KMAX>& C, int lane, bool act) {
+  constexpr int kCap = L2LWarpSmem<KMAX>::kCap;
+  float b[kQF];
 #pragma unroll
-  for (int t = 0; t < kQCap; ++t) b[t] = t < qn ? q[t][lane] : kKeyInf;
-  n_queued += qn;
-  qn = 0;
-  T.template merge<kQCap>(b);
-  return act ? T.thr() : -INFINITY;
+  for (int t = 0; t < kQF; ++t) {
+    const int r = C.nm + t < C.nb ? C.nm + t : 0;  // index stays inside the lane's buffer
+    const float v = __uint_as_float(buf[r < kCap ? r : 0][lane].x);
+    b[t] = C.nm + t < C.nb ? v : INFINITY;
+  }
+  C.pushed += (uint32_t)(C.nb - C.nm);
+  C.nm = C.nb;
+  C.F.template merge<kQF>(b);
+  C.thr = act ? C.F.t[KMAX - 1] : -INFINITY;
+}
+
+// Exact selection of the k best (d2, index) keys of a lane's buffer.
+template <int KMAX>
+__device__ __forceinline__ void select_exact(uint2 (*buf)[32], int nb, int k, int lane,
+                                             RegTopK<unsigned long long, KMAX>& T) {
+  T.init(k, 0ull, kKeyInf);
+  int mx = nb;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+  for (int r = 0; r < mx; r += 8) {
+    unsigned long long b[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i = r + t < nb ? r + t : 0;
+      const uint2 e = buf[i < L2LWarpSmem<KMAX>::kCap ? i : 0][lane];
+      b[t] = r + t < nb ? ((unsigned long long)e.x << 32) | (e.y + 1u) : kKeyInf;
+    }
+    T.template merge<8>(b);
+  }
+}
+
+// Keep only the buffer entries at or below thr.  If a lane still holds too many
+// (exact ties at the k-th distance), every lane also drops the tied entries
+// beyond its k best: fewer than k entries lie below thr, and of those at thr
+// the ones with the smallest indices are kept (indices are distinct).
+template <int KMAX>
+__device__ __forceinline__ void compact(uint2 (*buf)[32], Cand<KMAX>& C, int k, int lane) {
+  int w = 0;
+  for (int r = 0; r < C.nb; ++r) {
+    const uint2 e = buf[r][lane];
+    if (__uint_as_float(e.x) <= C.thr) buf[w++][lane] = e;
+  }
+  C.nb = C.nm = w;
+  if (!__any_sync(kFull, C.nb > L2LWarpSmem<KMAX>::kCap - 16)) return;
+  const uint32_t tb = __float_as_uint(C.thr);
+  int less = 0;
+  for (int r = 0; r < C.nb; ++r) less += __uint_as_float(buf[r][lane].x) < C.thr ? 1 : 0;
+  uint32_t cut = 0;
+  bool have = false;
+  for (int t = less; t < k; ++t) {  // the (k - less)-th smallest index among the ties
+    uint32_t mn = 0xffffffffu;
+    for (int r = 0; r < C.nb; ++r) {
+      const uint2 e = buf[r][lane];
+      if (e.x == tb && (!have || e.y > cut) && e.y < mn) mn = e.y;
+    }
+    cut = mn;
+    have = true;
+  }
+  w = 0;
+  for (int r = 0; r < C.nb; ++r) {
+    const uint2 e = buf[r][lane];
+    if (__uint_as_float(e.x) < C.thr || (have && e.x == tb && e.y <= cut)) buf[w++][lane] = e;
+  }
+  C.nb = C.nm = w;
 }
 
 // Per-leaf-pair distance mode (uniform over the warp): 0 plain, 1 fixed image
@@ -762,32 +841,66 @@ __device__ __forceinline__ float pair_d2(const float4& p, const float4& q, const
   return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
-// Scan one staged source leaf: every (query lane, source point) pair; distances
-// at or below the lane's k-th distance are queued, and the queues are merged
-// into the lists when any lane's queue is nearly full.
-template <int MODE, int K>
-__device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt, int G, int sub,
+// Distances from the lane's query to W staged source points: slot j0 + u*G + sub
+// (sub-lane sub of G lanes per query).  Slots past cnt read as NaN.
+template <int MODE, int W>
+__device__ __forceinline__ void window_d2(const float4* __restrict__ sp, int j0, int cnt, int G, int sub,
                                           const float4& qp, const float* sh, float L, float invL,
-                                          float& thr, int& qn, unsigned long long (*q)[32],
-                                          RegTopK<K>& T, int lane, bool act, uint32_t& n_queued) {
-  for (int j0 = 0; j0 < cnt; j0 += kUnroll * G) {
-    float d2[kUnroll];
-    int id[kUnroll];
+                                          float (&d2)[W], int (&id)[W]) {
+  if (G == 1) {  // j0 + u <= 31; the staged slots past cnt already hold NaN points
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int j = j0 + u * G + sub;  // slots past cnt hold +inf points
-      const float4 p = sp[j < 32 ? j : 31];
+    for (int u = 0; u < W; ++u) {
+      const float4 p = sp[j0 + u];
       d2[u] = pair_d2<MODE>(p, qp, sh, L, invL);
       id[u] = __float_as_int(p.w);
-      if (j >= 32) d2[u] = INFINITY;
     }
-    const float mn = fminf(fminf(d2[0], d2[1]), fminf(d2[2], d2[3]));
-    if (__any_sync(kFull, mn <= thr)) {
+  } else {
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        if (d2[u] <= thr) q[qn++][lane] = pack_key(d2[u], id[u]);
+    for (int u = 0; u < W; ++u) {
+      const int j = j0 + u * G + sub;
+      const float4 p = sp[j < 32 ? j : 31];
+      d2[u] = j < cnt ? pair_d2<MODE>(p, qp, sh, L, invL) : __int_as_float(0x7fffffff);
+      id[u] = __float_as_int(p.w);
+    }
+  }
+}
+
+// Scan one staged source leaf: every (query lane, source point) pair; points at
+// or below the lane's running k-th distance are appended to its buffer, and the
+// distance list (hence thr) is updated once a lane has more than kQF - W
+// unmerged entries.  One copy of the candidate code serves every image mode.
+template <bool PER, int KMAX>
+__device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt, int G, int sub, int mode,
+                                          const float4& qp, const float* sh, float L, float invL,
+                                          uint2 (*buf)[32], Cand<KMAX>& C, int k, int lane, bool act,
+                                          Meta* m) {
+  constexpr int kCap = L2LWarpSmem<KMAX>::kCap;
+  constexpr int W = 8;
+  static_assert(kQF >= W, "a window's candidates must fit the merge batch");
+  for (int j0 = 0; j0 < cnt; j0 += W * G) {
+    float d2[W];
+    int id[W];
+    if (!PER || mode == 0) window_d2<0, W>(sp, j0, cnt, G, sub, qp, sh, L, invL, d2, id);
+    else if (mode == 1) window_d2<1, W>(sp, j0, cnt, G, sub, qp, sh, L, invL, d2, id);
+    else window_d2<2, W>(sp, j0, cnt, G, sub, qp, sh, L, invL, d2, id);
+    float mn = d2[0];
+#pragma unroll
+    for (int u = 1; u < W; ++u) mn = fminf(mn, d2[u]);
+    if (__any_sync(kFull, mn <= C.thr)) {
+      // at a window's start C.nb <= kCap - W (the check below compacts
+      // otherwise), so the W slots from C.nb on are inside the buffer.  Every
+      // distance is written to slot C.nb and kept only if it passes (no
+      // divergent branch per source point); a rejected one is overwritten.
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        buf[C.nb][lane] = make_uint2(__float_as_uint(d2[u]), (uint32_t)id[u]);
+        C.nb += d2[u] <= C.thr ? 1 : 0;
       }
-      if (__any_sync(kFull, qn > kQCap - kUnroll)) thr = flush_queue<K>(q, T, lane, qn, act, n_queued);
+      if (__any_sync(kFull, C.nb - C.nm > kQF - W || C.nb > kCap - W)) {
+        if (C.nb > kCap) set_error(m, JZT_ERR_INTERNAL, kStageLeaf);  // cannot happen
+        merge_distances<KMAX>(buf, C, lane, act);
+        if (__any_sync(kFull, C.nb > kCap - W)) compact<KMAX>(buf, C, k, lane);
+      }
     }
   }
 }
@@ -805,10 +918,10 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
                                                            float L, int order,
                                                            int32_t* __restrict__ out_idx,
                                                            float* __restrict__ out_d2, Meta* m) {
-  __shared__ L2LWarpSmem S_all[kL2LWarps];
+  extern __shared__ __align__(16) unsigned char l2l_smem[];
   if (warp_failed(m)) return;
   const int w = warp_id(), lane = lane_id();
-  L2LWarpSmem& S = S_all[w];
+  L2LWarpSmem<KMAX>& S = reinterpret_cast<L2LWarpSmem<KMAX>*>(l2l_smem)[w];
   if (lane == 0) {
     for (int t = 0; t < kStages; ++t) mbar_init(&S.bar[t], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -830,13 +943,13 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
     const int qi = lane / G, sub = lane & (G - 1);
     const bool act = qi < q;
     const float4 qp = act ? pts[me.first + qi] : make_float4(0.f, 0.f, 0.f, 0.f);
-    RegTopK<KMAX> T;
-    T.init(k);
-    float thr = act ? INFINITY : -INFINITY;
-    int qn = 0;
+    Cand<KMAX> C;
+    C.F.init(k, -INFINITY, INFINITY);
+    C.nb = C.nm = 0;
+    C.thr = act ? INFINITY : -INFINITY;
+    C.pushed = 0;
     unsigned long long pairs = 0;
     unsigned long long st_examined = 0, st_scanned = 0;
-    uint32_t n_queued = 0;
     const uint2 lo = ilo[leaf];
     const uint32_t e_cnt = lo.y & ~kUnsortedBit;
     const bool sorted = (lo.y & kUnsortedBit) == 0;
@@ -845,33 +958,39 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
 
     for (uint32_t b0 = 0; b0 < e_cnt && !broken && !stop; b0 += 32) {
       const uint32_t nb = min(32u, e_cnt - b0);
-      // metadata of up to 32 entries, one per lane
-      IEntry en;
-      en.src = 0;
-      en.r2low = INFINITY;
-      NodeRec sr;
+      // metadata of up to 32 entries, one entry per lane, into shared memory:
+      // source box (moved to the periodic image chosen for the whole leaf pair),
+      // r_low^2, point range and image mode; read back by broadcast loads
       if ((uint32_t)lane < nb) {
-        en = list[b0 + lane];
+        IEntry en = list[b0 + lane];
         if ((uint64_t)(uint32_t)en.src >= (uint64_t)nl) {  // consistency guard
           set_error(m, JZT_ERR_INTERNAL, kStageLeaf);
           en.src = 0;
           en.r2low = INFINITY;
         }
-        sr = leaves[en.src];
-      } else {
-        sr.count = 0;
-        sr.first = 0;
-        sr.lo[0] = sr.lo[1] = sr.lo[2] = sr.hi[0] = sr.hi[1] = sr.hi[2] = 0.0f;
+        const NodeRec sr = leaves[en.src];
+        float sh[3] = {0.0f, 0.0f, 0.0f};
+        const int mode = pair_mode<PER>(me, sr.lo, sr.hi, L, sh);
+        float bl[3], bh[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          bl[d] = PER && mode == 1 ? __fadd_rd(sr.lo[d], sh[d]) : sr.lo[d];
+          bh[d] = PER && mode == 1 ? __fadd_ru(sr.hi[d], sh[d]) : sr.hi[d];
+        }
+        S.meta[lane][0] = make_float4(bl[0], bl[1], bl[2], en.r2low);
+        S.meta[lane][1] = make_float4(bh[0], bh[1], bh[2], __int_as_float(sr.first));
+        S.meta[lane][2] = make_float4(sh[0], sh[1], sh[2], __int_as_float(sr.count | (mode << 8)));
       }
+      __syncwarp();
       uint32_t issued = 0, done = 0;
       auto issue = [&](uint32_t e) {
-        const float r2 = __shfl_sync(kFull, en.r2low, e);
-        if (sorted && !__any_sync(kFull, act && r2 <= thr)) {
+        const float r2 = S.meta[e][0].w;
+        if (sorted && !__any_sync(kFull, act && r2 <= C.thr)) {
           stop = true;
           return;
         }
-        const int first = __shfl_sync(kFull, sr.first, e);
-        const int cnt = __shfl_sync(kFull, sr.count, e);
+        const int first = __float_as_int(S.meta[e][1].w);
+        const int cnt = __float_as_int(S.meta[e][2].w) & 0xff;
         const int st = e % kStages;
         __syncwarp();
         if (lane == 0) {
@@ -899,57 +1018,45 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
         parity ^= 1u << st;
         ++done;
         ++st_examined;
-        const int cnt = __shfl_sync(kFull, sr.count, e);
-        // pad the stage with far-away points so the unrolled scan needs no bounds
-        if (lane >= cnt)
-          S.pts[st][lane] = make_float4(INFINITY, INFINITY, INFINITY, __int_as_float(INT_MAX));
+        const float4 m0 = S.meta[e][0], m1 = S.meta[e][1], m2 = S.meta[e][2];
+        const int cnt = __float_as_int(m2.w) & 0xff;
+        const int mode = __float_as_int(m2.w) >> 8;
+        // pad the stage with NaN points (their distances fail every test)
+        if (lane >= cnt) S.pts[st][lane] = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff),
+                                                       __int_as_float(0x7fffffff), __int_as_float(INT_MAX));
         __syncwarp();
-        const float r2 = __shfl_sync(kFull, en.r2low, e);
-        bool skip = !__any_sync(kFull, act && r2 <= thr);
+        bool skip = !__any_sync(kFull, act && m0.w <= C.thr);
         if (skip && sorted) stop = true;
-        float bl[3], bh[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          bl[d] = __shfl_sync(kFull, sr.lo[d], e);
-          bh[d] = __shfl_sync(kFull, sr.hi[d], e);
-        }
-        float sh[3] = {0.0f, 0.0f, 0.0f};
-        int mode = 0;
+        const float sh[3] = {m2.x, m2.y, m2.z};
         if (!skip) {
-          // point-to-box lower bound against this lane's threshold, using the
-          // image chosen for the whole leaf pair (all three only when ambiguous)
-          mode = pair_mode<PER>(me, bl, bh, L, sh);
-          float pb = 0.0f;
+          // point-to-box lower bound against this lane's threshold, in the image
+          // chosen for the whole leaf pair (all three images when ambiguous)
           const float qq[3] = {qp.x, qp.y, qp.z};
+          const float bl[3] = {m0.x, m0.y, m0.z}, bh[3] = {m1.x, m1.y, m1.z};
+          float pb = 0.0f;
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            float g;
-            if (PER && mode == 2) {
-              g = gap_rd_per(qq[d], qq[d], bl[d], bh[d], L);
-            } else {
-              const float lo_d = PER ? __fadd_rd(bl[d], sh[d]) : bl[d];
-              const float hi_d = PER ? __fadd_ru(bh[d], sh[d]) : bh[d];
-              g = fmaxf(0.0f, fmaxf(__fsub_rd(lo_d, qq[d]), __fsub_rd(qq[d], hi_d)));
-            }
+            const float g = PER && mode == 2
+                                ? gap_rd_per(qq[d], qq[d], bl[d], bh[d], L)
+                                : fmaxf(0.0f, fmaxf(__fsub_rd(bl[d], qq[d]), __fsub_rd(qq[d], bh[d])));
             pb = __fmaf_rd(g, g, pb);
           }
-          skip = !__any_sync(kFull, act && pb * kLowSlack <= thr);
+          skip = !__any_sync(kFull, act && pb * kLowSlack <= C.thr);
         }
         if (!skip) {
           pairs += (unsigned long long)q * (unsigned long long)cnt;
           ++st_scanned;
-          if (mode == 0)
-            scan_leaf<0, KMAX>(S.pts[st], cnt, G, sub, qp, sh, L, invL, thr, qn, S.q, T, lane, act, n_queued);
-          else if (mode == 1)
-            scan_leaf<1, KMAX>(S.pts[st], cnt, G, sub, qp, sh, L, invL, thr, qn, S.q, T, lane, act, n_queued);
-          else
-            scan_leaf<2, KMAX>(S.pts[st], cnt, G, sub, qp, sh, L, invL, thr, qn, S.q, T, lane, act, n_queued);
+          scan_leaf<PER, KMAX>(S.pts[st], cnt, G, sub, mode, qp, sh, L, invL, S.buf, C, k, lane, act, m);
         }
         __syncwarp();
         if (!stop && issued < nb) issue(issued);
       }
     }
-    thr = flush_queue<KMAX>(S.q, T, lane, qn, act, n_queued);
+    // final k-th distance, drop the entries beyond it, exact (d2, index) selection
+    merge_distances<KMAX>(S.buf, C, lane, act);
+    compact<KMAX>(S.buf, C, k, lane);
+    RegTopK<unsigned long long, KMAX> T;
+    select_exact<KMAX>(S.buf, C.nb, k, lane, T);
     __syncwarp();
     // merge the G partial lists of each query (butterfly over the sub-lanes)
     for (int st = 1; st < G; st <<= 1) {
@@ -967,7 +1074,7 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
       atomicAdd(&m->knn_stats[1], st_scanned);
     }
     {
-      unsigned long long a = n_queued;
+      unsigned long long a = C.pushed;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
       if (lane == 0) atomicAdd(&m->knn_stats[2], a);
@@ -1023,7 +1130,9 @@ void l2l_knn(const Layout& L, char* ws, int k, float pl, int order, int32_t* idx
              cudaStream_t s) {
   Meta* m = at<Meta>(ws, L.meta);
   const int sms = 152;
-  k_l2l_knn<KMAX, PER><<<sms * 8, 32 * kL2LWarps, 0, s>>>(
+  const size_t smem = sizeof(L2LWarpSmem<KMAX>) * kL2LWarps;
+  cudaFuncSetAttribute(k_l2l_knn<KMAX, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_l2l_knn<KMAX, PER><<<sms * 8, 32 * kL2LWarps, smem, s>>>(
       at<float4>(ws, L.pts), at<NodeRec>(ws, L.nodes[0]), at<uint2>(ws, L.ilo[0]),
       at<IEntry>(ws, L.arena), k, pl, order, idx, d2, m); note_launch();
 }
