@@ -351,7 +351,9 @@ struct SortSmem {
   uint32_t stage_v[kSortTile];
 };
 
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint64_t* __restrict__ kin,
+constexpr int kLookWin = 8;  // predecessor words read per look-back step
+
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __restrict__ kin,
                                                            const uint32_t* __restrict__ vin,
                                                            uint64_t* __restrict__ kout,
                                                            uint32_t* __restrict__ vout, int64_t n,
@@ -420,22 +422,38 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint64_t* __res
       S.gbase[d] = m->radix_offsets[pass][d];
     } else {
       st_release_u32(&lb[d], kFlagA | count);
+      // walk back over the predecessors' (flag | count) words, kLookWin at a
+      // time (independent loads): add aggregates (A) until an inclusive prefix
+      // (P) is found; stop at an unpublished word and reload from there
       uint32_t excl = 0;
       int64_t j = tile - 1;
       long long spins = 0;
-      while (j >= 0) {
-        uint32_t v = ld_acquire_u32(lookback + (size_t)j * kRadixBins + d);
-        uint32_t f = v & ~kValMask;
-        if (f == 0) {
-          if (++spins > kSpinLimit || failed(m)) {
-            set_error(m, JZT_ERR_TIMEOUT, kStageSort);
-            break;
+      bool found = false;
+      while (!found && j >= 0) {
+        uint32_t v[kLookWin];
+#pragma unroll
+        for (int i = 0; i < kLookWin; ++i)
+          v[i] = j - i >= 0 ? ld_relaxed_u32(lookback + (size_t)(j - i) * kRadixBins + d) : kFlagP;
+        int used = 0;
+        bool blocked = false;
+#pragma unroll
+        for (int i = 0; i < kLookWin; ++i) {
+          if (found || blocked) continue;
+          const uint32_t f = v[i] & ~kValMask;
+          if (f == 0) {
+            blocked = true;
+            continue;
           }
-          continue;
+          excl += v[i] & kValMask;
+          ++used;
+          if (f == kFlagP) found = true;
         }
-        excl += v & kValMask;
-        if (f == kFlagP) break;
-        --j;
+        j -= used;
+        if (blocked && ++spins > kSpinLimit) {
+          set_error(m, JZT_ERR_TIMEOUT, kStageSort);
+          break;
+        }
+        if (blocked && failed(m)) break;
       }
       st_release_u32(&lb[d], kFlagP | (excl + count));
       S.gbase[d] = m->radix_offsets[pass][d] + excl;
