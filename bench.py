@@ -33,6 +33,9 @@ FP32_LANES_PER_SM = 128
 SMS = 152
 SORT_BYTES_PER_PT = 24    # one LSD pass: read key+value, write key+value (8+4 each way)
 BUILD_FLOOR_BYTES = 42    # read xyz 12 + sorted float4 16 + keys/perm 12 + tree ~2
+# DRAM bytes per point of one k_l2l_knn launch (k = 16): 695 MB read + 2094 MB written
+# on 2^24 points, from the ncu capture of this kernel version
+L2L_TRAFFIC_BYTES_PER_PT = (695.3e6 + 2094.0e6) / (1 << 24)
 
 
 def parse():
@@ -44,7 +47,7 @@ def parse():
     ap.add_argument("--n-side", type=int, default=512)
     ap.add_argument("--k", type=int, default=16)
     ap.add_argument("--b-frac", type=float, default=0.2)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--ref-side", type=float, default=0.25,
                     help="side of the sub-cube timed per step by --impl reference")
     ap.add_argument("--cpu-side", type=float, default=0.75,
@@ -405,39 +408,78 @@ def main():
         ms_step = float(t.item())
     value = world * n / (ms_step / 1000.0)
 
-    # end to end through host buffers (pinned): input H2D, outputs D2H, every step
-    e2e = None
+    del ws, idx, d2, lab, tree
+    torch.cuda.empty_cache()
+
+    # end to end from pinned host buffers: every step uploads its points and reads
+    # back kNN rows and FoF labels.  HostPipeline overlaps the transfers of one
+    # step with the compute of its neighbours (double-buffered device buffers);
+    # e2e_serial runs the same steps strictly one after another on one stream.
+    e2e, e2e_serial = None, None
     if a.e2e_steps > 0:
+        from paper_2604_05885_gb300.pipeline import HostPipeline
         try:
             x_host = torch.from_numpy(x).pin_memory()
             idx_h = torch.empty((n, k), dtype=torch.int32).pin_memory()
             d2_h = torch.empty((n, k), dtype=torch.float32).pin_memory()
             lab_h = torch.empty(n, dtype=torch.int32).pin_memory()
-            x_in = torch.empty_like(x_dev)
+        except RuntimeError as exc:  # pinned allocation refused
+            x_host = None
+            e2e = {"value": None, "unit": UNIT, "error": str(exc)[:200]}
+        if x_host is not None:
+            h2d = x_host.numel() * 4
+            d2h = idx_h.numel() * 4 + d2_h.numel() * 4 + lab_h.numel() * 4
+            pipe = HostPipeline(n, k, b, L, params, dev)
+            for _ in range(2):
+                pipe.submit(x_host, idx_h, d2_h, lab_h)
+            pipe.synchronize()
             barrier()
             f0 = torch.cuda.Event(enable_timing=True)
             f1 = torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
+            f0.record(pipe.s_up)
             for _ in range(a.e2e_steps):
-                x_in.copy_(x_host, non_blocking=True)
-                step(x_in)
-                idx_h.copy_(idx, non_blocking=True)
-                d2_h.copy_(d2, non_blocking=True)
-                lab_h.copy_(lab, non_blocking=True)
-            f1.record(stream)
+                pipe.submit(x_host, idx_h, d2_h, lab_h)
+            f1.record(pipe.s_down)
+            pipe.synchronize()
             barrier()
             ms_e2e = f0.elapsed_time(f1) / a.e2e_steps
+            pipe.status(raise_on_error=True)
+            del pipe
+            torch.cuda.empty_cache()
+            # serial: one stream, upload -> compute -> download per step
+            ws1 = jzt.alloc_workspace(n, k, params, dev)
+            x_in = torch.empty((n, 3), dtype=torch.float32, device=dev)
+            i1 = torch.empty((n, k), dtype=torch.int32, device=dev)
+            d1 = torch.empty((n, k), dtype=torch.float32, device=dev)
+            l1 = torch.empty(n, dtype=torch.int32, device=dev)
+            barrier()
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(max(1, a.e2e_steps // 2)):
+                x_in.copy_(x_host, non_blocking=True)
+                t1 = jzt.build(x_in, periodic_L=L, workspace=ws1, params=params)
+                t1.knn(k, out=(i1, d1))
+                t1.fof(b, out=l1)
+                idx_h.copy_(i1, non_blocking=True)
+                d2_h.copy_(d1, non_blocking=True)
+                lab_h.copy_(l1, non_blocking=True)
+            g1.record(stream)
+            barrier()
+            ms_ser = g0.elapsed_time(g1) / max(1, a.e2e_steps // 2)
+            t1.status(raise_on_error=True)
+            del ws1, x_in, i1, d1, l1, t1
+            torch.cuda.empty_cache()
             if dist is not None:
-                t = torch.tensor([ms_e2e], device=dev)
+                t = torch.tensor([ms_e2e, ms_ser], device=dev)
                 dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                ms_e2e = float(t.item())
-            h2d = x_host.numel() * 4
-            d2h = idx_h.numel() * 4 + d2_h.numel() * 4 + lab_h.numel() * 4
+                ms_e2e, ms_ser = float(t[0].item()), float(t[1].item())
             e2e = {"value": world * n / (ms_e2e / 1000.0), "unit": UNIT, "ms_per_step": ms_e2e,
-                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-            jzt.profile_read()
-        except RuntimeError as exc:  # pinned allocation refused
-            e2e = {"value": None, "unit": UNIT, "error": str(exc)[:200]}
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "mode": "HostPipeline: transfers of neighbouring steps overlap the compute"}
+            e2e_serial = {"value": world * n / (ms_ser / 1000.0), "unit": UNIT, "ms_per_step": ms_ser,
+                          "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        jzt.profile_read()
 
     # rooflines ----------------------------------------------------------------
     peaks = {}
@@ -456,7 +498,9 @@ def main():
     achieved = pairs_per_launch * FLOPS_PER_PAIR / (l2l_ms / 1000.0) / 1e12 if l2l_ms else 0.0
     roofline = {"kernel": "k_l2l_knn", "bound": "alu", "achieved": achieved, "peak": alu_peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / alu_peak_tflops if alu_peak_tflops else None,
-                "traffic": None, "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock sampled)",
+                "traffic": L2L_TRAFFIC_BYTES_PER_PT * n if (n_side == 512 and k == 16) else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_l2l_knn on the 256^3 "
+                                  "set (profiles/k_l2l_knn_zeldovich256.md), scaled by N", "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock sampled)",
                 "work": f"{pairs_per_launch} point pairs x {FLOPS_PER_PAIR} flops per launch",
                 "ms_per_launch": l2l_ms}
     sort_ms = phase_ms.get("sort", 0.0) / max(1, phase_cnt.get("sort", 0))
@@ -478,7 +522,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
-            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "clocks": clk, "e2e": e2e, "e2e_serial": e2e_serial, "gpu_launches": launches, "roofline": roofline,
             "roofline_sort": roof_sort, "roofline_build": roof_build,
             "phases_ms_per_step": {ph: phase_ms[ph] / steps for ph in phase_ms},
             "knn_particles_per_s": n / ((build_ms + knn_ms) / 1000.0) if knn_ms else None,
@@ -489,7 +533,7 @@ def main():
             "knn_l2l_entries_examined": st["knn_stats"][0], "knn_l2l_leaves_scanned": st["knn_stats"][1],
             "knn_l2l_candidates_queued": st["knn_stats"][2], "knn_l2l_heap_insertions": st["knn_stats"][3],
             "p50_p99_latency": None}
-    del ws, idx, d2, lab, x_dev, tree
+    del x_dev
     torch.cuda.synchronize(dev)
     torch.cuda.empty_cache()
 

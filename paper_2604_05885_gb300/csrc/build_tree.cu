@@ -413,15 +413,17 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __
   uint32_t total;
   uint32_t start = block_excl_scan<kSortThreads>(count, &total);
   S.tile_start[t] = start;
-  // decoupled look-back, one digit per thread
+  // decoupled look-back, one digit per thread.  Each published word carries
+  // its own flag and count and nothing else is published through it, so the
+  // stores and loads are relaxed (no fences)
   {
     const int d = t;
     uint32_t* lb = lookback + (size_t)tile * kRadixBins;
     if (tile == 0) {
-      st_release_u32(&lb[d], kFlagP | count);
+      st_relaxed_u32(&lb[d], kFlagP | count);
       S.gbase[d] = m->radix_offsets[pass][d];
     } else {
-      st_release_u32(&lb[d], kFlagA | count);
+      st_relaxed_u32(&lb[d], kFlagA | count);
       // walk back over the predecessors' (flag | count) words, kLookWin at a
       // time (independent loads): add aggregates (A) until an inclusive prefix
       // (P) is found; stop at an unpublished word and reload from there
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __
         }
         if (blocked && failed(m)) break;
       }
-      st_release_u32(&lb[d], kFlagP | (excl + count));
+      st_relaxed_u32(&lb[d], kFlagP | (excl + count));
       S.gbase[d] = m->radix_offsets[pass][d] + excl;
     }
   }
