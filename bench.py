@@ -306,22 +306,48 @@ def serving_run(a, dev, log):
             "load_sweep": sweep or None}
 
 
-def dist_setup(gpus):
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+def dist_env():
+    """(rank, world size, local rank) from the torchrun environment (1 process: 0, 1, 0)."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def dist_setup(backend="nccl"):
+    """One process per GPU: a process group when there is more than one rank.
+    The ranks are independent replicas; the group only carries the barriers
+    and the max-over-ranks timing."""
+    rank, world, local = dist_env()
     pg = None
     if world > 1:
         import torch.distributed as dist
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend)
         pg = dist
     return rank, world, local, pg
 
 
+def max_over_ranks(values, dist, device="cpu"):
+    """Element-wise maximum of a list of floats over all ranks (identity for one rank)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Replicas: every rank processes units_per_rank; the job's rate uses the slowest rank."""
+    return world * units_per_rank / (ms_max / 1000.0)
+
+
 def main():
     a = parse()
-    rank, world, local, dist = dist_setup(a.gpus)
+    if a.impl == "reference":
+        rank, world, local = dist_env()
+        dist = None  # rank 0 alone times the oracle; the other ranks exit without work
+    else:
+        rank, world, local, dist = dist_setup("nccl")
     n_side = a.n_side
     n = n_side ** 3
     k = a.k
@@ -401,12 +427,8 @@ def main():
     ms_total = e0.elapsed_time(e1)
     phase_ms, phase_cnt, launches = jzt.profile_read()
     st = tree.status(raise_on_error=True)
-    ms_step = ms_total / a.steps
-    if dist is not None:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * n / (ms_step / 1000.0)
+    ms_step = max_over_ranks([ms_total / a.steps], dist, dev)[0]
+    value = whole_job_rate(n, world, ms_step)
 
     del ws, idx, d2, lab, tree
     torch.cuda.empty_cache()
@@ -470,14 +492,11 @@ def main():
             t1.status(raise_on_error=True)
             del ws1, x_in, i1, d1, l1, t1
             torch.cuda.empty_cache()
-            if dist is not None:
-                t = torch.tensor([ms_e2e, ms_ser], device=dev)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                ms_e2e, ms_ser = float(t[0].item()), float(t[1].item())
-            e2e = {"value": world * n / (ms_e2e / 1000.0), "unit": UNIT, "ms_per_step": ms_e2e,
+            ms_e2e, ms_ser = max_over_ranks([ms_e2e, ms_ser], dist, dev)
+            e2e = {"value": whole_job_rate(n, world, ms_e2e), "unit": UNIT, "ms_per_step": ms_e2e,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "mode": "HostPipeline: transfers of neighbouring steps overlap the compute"}
-            e2e_serial = {"value": world * n / (ms_ser / 1000.0), "unit": UNIT, "ms_per_step": ms_ser,
+            e2e_serial = {"value": whole_job_rate(n, world, ms_ser), "unit": UNIT, "ms_per_step": ms_ser,
                           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         jzt.profile_read()
 

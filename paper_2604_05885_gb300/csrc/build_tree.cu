@@ -353,7 +353,7 @@ struct SortSmem {
 
 constexpr int kLookWin = 8;  // predecessor words read per look-back step
 
-__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const uint64_t* __restrict__ kin,
+__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const uint64_t* __restrict__ kin,
                                                            const uint32_t* __restrict__ vin,
                                                            uint64_t* __restrict__ kout,
                                                            uint32_t* __restrict__ vout, int64_t n,

@@ -18,7 +18,7 @@ constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kRadixPasses = (3 * kKeyBits + kRadixBits - 1) / kRadixBits;  // 8
 constexpr int kSortThreads = 256;
-constexpr int kSortIpt = 16;
+constexpr int kSortIpt = 12;
 constexpr int kSortTile = kSortThreads * kSortIpt;  // 4096 keys per tile
 constexpr int kScanTile = 1024;                      // elements per compaction tile
 constexpr int kMaxK = 32;
