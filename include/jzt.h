@@ -83,8 +83,8 @@ typedef struct jzt_status_info {
 } jzt_status_info;
 
 /* Workspace size for N points and parameters p (NULL = defaults).  k_or_0 is the
- * largest k the caller will ask for (0 if only FoF): the interaction-list part
- * grows with k above 16.  The interaction-list arena is the last part of the
+ * largest k the caller will ask for (0 if only FoF, at most 256): the
+ * interaction-list part grows with k above 16.  The interaction-list arena is the last part of the
  * workspace and takes all of it that remains, so a caller that gets
  * JZT_ERR_CAPACITY can retry with a larger workspace (see
  * jzt_status_info.required_bytes) and the same parameters.  Host-only.
@@ -108,8 +108,12 @@ int jzt_build(const float *d_xyz, int64_t n, float periodic_L, const jzt_params 
  * neighbours by original index, ascending by (float32 squared distance, index).
  * order: 0 = rows in input order (Sec. III-E final reordering), 1 = rows in z order
  * (row r belongs to the point at sorted position r, whose original index is the
- * .w lane of jzt_tree_arrays' pts).
- * Errors: JZT_ERR_INVALID (k < 1, k > N, null outputs), JZT_ERR_UNSUPPORTED (k > 32). */
+ * .w lane of jzt_tree_arrays' pts).  k up to 32 takes one LeafToLeaf pass; larger
+ * k (up to 256) takes ceil(k / 32) passes over the same interaction lists, pass j
+ * keeping the next 32 keys above the last key of pass j - 1 (the lower radius and
+ * index offset of Sec. III-B's repeated LeafToLeaf); the workspace must have been
+ * sized for this k (jzt_workspace_bytes), else JZT_ERR_CAPACITY.
+ * Errors: JZT_ERR_INVALID (k < 1, k > N, null outputs), JZT_ERR_UNSUPPORTED (k > 256). */
 int jzt_tree_knn(jzt_tree *t, int k, int order, int32_t *d_idx, float *d_dist2, void *stream);
 
 /* FoF groups at linking length b (Sec. IV): points i, j are friends when their
@@ -160,7 +164,7 @@ typedef struct jzt_job {
     int64_t n;            /* 1 <= N < 2^30 */
     float periodic_L;     /* > 0: periodic box [0,L)^3 */
     int32_t op;           /* JZT_OP_KNN or JZT_OP_FOF */
-    int32_t k;            /* kNN: neighbours per point, 1..min(32, N) */
+    int32_t k;            /* kNN: neighbours per point, 1..min(256, N) */
     float b;              /* FoF: linking length */
     int32_t lane;         /* lane (0 <= lane < n_lanes) that runs the job */
     int32_t pad;

@@ -178,7 +178,7 @@ const char* jzt_version(void) { return "jzt-gb300 0.1.0 (sm_103a)"; }
 int jzt_workspace_bytes(int64_t n, int k_or_0, const jzt_params* p, size_t* bytes) {
   if (!bytes) return fail(JZT_ERR_INVALID, "bytes is null");
   if (int e = check_n(n)) return e;
-  if (k_or_0 < 0 || k_or_0 > kMaxK) return fail(JZT_ERR_INVALID, "k_or_0 must be in 0..32");
+  if (k_or_0 < 0 || k_or_0 > kMaxKTotal) return fail(JZT_ERR_INVALID, "k_or_0 must be in 0..256");
   Params P;
   const char* why = nullptr;
   if (int e = resolve_params(p, &P, &why)) return fail(e, why);
@@ -225,7 +225,7 @@ int jzt_tree_knn(jzt_tree* t, int k, int order, int32_t* d_idx, float* d_dist2, 
   if (!t) return fail(JZT_ERR_INVALID, "tree is null");
   if (!d_idx || !d_dist2) return fail(JZT_ERR_INVALID, "null output pointer");
   if (k < 1 || (int64_t)k > t->n) return fail(JZT_ERR_INVALID, "k must satisfy 1 <= k <= N");
-  if (k > kMaxK) return fail(JZT_ERR_UNSUPPORTED, "k > 32 is not supported");
+  if (k > kMaxKTotal) return fail(JZT_ERR_UNSUPPORTED, "k > 256 is not supported");
   if (order != 0 && order != 1) return fail(JZT_ERR_INVALID, "order must be 0 (input) or 1 (z)");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   launch_knn(t->L, t->ws, t->periodic_L, k, order, d_idx, d_dist2, s);
@@ -249,8 +249,8 @@ int jzt_tree_fof(jzt_tree* t, float b, int32_t* d_labels, void* stream) {
 
 int jzt_knn(const float* d_xyz, int64_t n, int k, float periodic_L, int32_t* d_idx, float* d_dist2,
             void* d_ws, size_t ws_bytes, void* stream) {
-  if (k < 1 || k > kMaxK || (int64_t)k > n) {
-    if (k > kMaxK && (int64_t)k <= n) return fail(JZT_ERR_UNSUPPORTED, "k > 32 is not supported");
+  if (k < 1 || k > kMaxKTotal || (int64_t)k > n) {
+    if (k > kMaxKTotal && (int64_t)k <= n) return fail(JZT_ERR_UNSUPPORTED, "k > 256 is not supported");
     return fail(JZT_ERR_INVALID, "k must satisfy 1 <= k <= N");
   }
   if (!d_idx || !d_dist2) return fail(JZT_ERR_INVALID, "null output pointer");

@@ -51,7 +51,7 @@ extern "C" int jzt_batch_run(const jzt_job* jobs, int n_jobs, const jzt_params* 
     if (J.op == JZT_OP_KNN) {
       if (!J.d_idx || !J.d_dist2) return fail_msg(JZT_ERR_INVALID, tag + "null kNN outputs");
       if (J.k < 1 || (int64_t)J.k > J.n) return fail_msg(JZT_ERR_INVALID, tag + "k must satisfy 1 <= k <= N");
-      if (J.k > kMaxK) return fail_msg(JZT_ERR_UNSUPPORTED, tag + "k > 32 is not supported");
+      if (J.k > kMaxKTotal) return fail_msg(JZT_ERR_UNSUPPORTED, tag + "k > 256 is not supported");
     } else if (J.op == JZT_OP_FOF) {
       if (!J.d_labels) return fail_msg(JZT_ERR_INVALID, tag + "null FoF labels");
       if (!(J.b > 0.0f) || std::isinf(J.b)) return fail_msg(JZT_ERR_INVALID, tag + "b must be positive and finite");

@@ -21,7 +21,8 @@ constexpr int kSortThreads = 256;
 constexpr int kSortIpt = 12;
 constexpr int kSortTile = kSortThreads * kSortIpt;  // 4096 keys per tile
 constexpr int kScanTile = 1024;                      // elements per compaction tile
-constexpr int kMaxK = 32;
+constexpr int kMaxK = 32;        // neighbours per LeafToLeaf pass
+constexpr int kMaxKTotal = 256;  // neighbours per query (passes of kMaxK; one walk counter each)
 constexpr int kCtrLeafSplits = 8;
 constexpr int kCtrCoarse = 9;   // + plane
 constexpr int kCtrWalk = 24;

@@ -636,15 +636,11 @@ __device__ __forceinline__ float point_box_d2(float4 q, const NodeRec& b, float 
 constexpr int kQF = JZT_L2L_QF;          // buffered candidates per lane between threshold updates
 constexpr int kL2LWarps = 4;
 constexpr int kStages = JZT_L2L_STAGES;  // source leaves in flight per warp
-constexpr int kUnroll = 4;               // source points per vote
 
-// Candidates are packed as (float32 bits of d2) << 32 | (original index + 1):
+// Exact keys are packed as (float32 bits of d2) << 32 | (original index + 1):
 // for d2 >= 0 the unsigned order of the key is the order by (d2, index), and 0
 // is below every real key (used to pad lists for k below the list size).
 constexpr unsigned long long kKeyInf = ~0ull;
-__device__ __forceinline__ unsigned long long pack_key(float d2, int idx) {
-  return ((unsigned long long)__float_as_uint(d2) << 32) | (uint32_t)(idx + 1);
-}
 
 // Per-warp shared memory: staged source leaves and, per lane, a buffer of
 // candidate (d2 bits, original index) pairs.  The buffer holds KMAX + 32
@@ -869,11 +865,11 @@ __device__ __forceinline__ void window_d2(const float4* __restrict__ sp, int j0,
 // or below the lane's running k-th distance are appended to its buffer, and the
 // distance list (hence thr) is updated once a lane has more than kQF - W
 // unmerged entries.  One copy of the candidate code serves every image mode.
-template <bool PER, int KMAX>
+template <bool PER, bool LB, int KMAX>
 __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt, int G, int sub, int mode,
                                           const float4& qp, const float* sh, float L, float invL,
                                           uint2 (*buf)[32], Cand<KMAX>& C, int k, int lane, bool act,
-                                          Meta* m) {
+                                          float lb_d2, int lb_id, Meta* m) {
   constexpr int kCap = L2LWarpSmem<KMAX>::kCap;
   constexpr int W = 8;
   static_assert(kQF >= W, "a window's candidates must fit the merge batch");
@@ -894,7 +890,9 @@ __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt
 #pragma unroll
       for (int u = 0; u < W; ++u) {
         buf[C.nb][lane] = make_uint2(__float_as_uint(d2[u]), (uint32_t)id[u]);
-        C.nb += d2[u] <= C.thr ? 1 : 0;
+        bool keep = d2[u] <= C.thr;
+        if (LB) keep = keep && (d2[u] > lb_d2 || (d2[u] == lb_d2 && id[u] > lb_id));
+        C.nb += keep ? 1 : 0;
       }
       if (__any_sync(kFull, C.nb - C.nm > kQF - W || C.nb > kCap - W)) {
         if (C.nb > kCap) set_error(m, JZT_ERR_INTERNAL, kStageLeaf);  // cannot happen
@@ -910,11 +908,18 @@ __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt
 // the list metadata (source box and point range) is read 32 entries at a time,
 // one entry per lane.  Each query lane keeps its k best (d2, index) keys in a
 // sorted register list (RegTopK); its last key is the running k-th distance.
-template <int KMAX, bool PER>
+//
+// k above 32 runs several passes (LB = true after the first): pass j fills the
+// row's columns col0 = 32 j .. col0 + k - 1 (row length k_row) with the k best
+// keys strictly above the last key of pass j - 1, read back from the output
+// (so exact ties continue in index order).  The interaction lists, built for
+// all k_row neighbours, serve every pass.
+template <int KMAX, bool PER, bool LB>
 __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l_knn(const float4* __restrict__ pts,
                                                            const NodeRec* __restrict__ leaves,
                                                            const uint2* __restrict__ ilo,
                                                            const IEntry* __restrict__ arena, int k,
+                                                           int k_row, int col0, int ctr,
                                                            float L, int order,
                                                            int32_t* __restrict__ out_idx,
                                                            float* __restrict__ out_d2, Meta* m) {
@@ -933,7 +938,7 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
   bool broken = false;
   while (!broken) {
     int64_t leaf = 0;
-    if (lane == 0) leaf = atomicAdd(&m->tile_ctr[kCtrWalk], 1u);
+    if (lane == 0) leaf = atomicAdd(&m->tile_ctr[ctr], 1u);
     leaf = __shfl_sync(kFull, leaf, 0);
     if (leaf >= nl) break;
     const NodeRec me = leaves[leaf];
@@ -948,6 +953,13 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
     C.nb = C.nm = 0;
     C.thr = act ? INFINITY : -INFINITY;
     C.pushed = 0;
+    float lb_d2 = -INFINITY;  // lower bound key (previous pass's last), LB only
+    int lb_id = -1;
+    if (LB && act) {
+      const int64_t row = order == 0 ? (int64_t)__float_as_int(qp.w) : (int64_t)(me.first + qi);
+      lb_d2 = out_d2[row * k_row + col0 - 1];
+      lb_id = out_idx[row * k_row + col0 - 1];
+    }
     unsigned long long pairs = 0;
     unsigned long long st_examined = 0, st_scanned = 0;
     const uint2 lo = ilo[leaf];
@@ -1046,7 +1058,8 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
         if (!skip) {
           pairs += (unsigned long long)q * (unsigned long long)cnt;
           ++st_scanned;
-          scan_leaf<PER, KMAX>(S.pts[st], cnt, G, sub, mode, qp, sh, L, invL, S.buf, C, k, lane, act, m);
+          scan_leaf<PER, LB, KMAX>(S.pts[st], cnt, G, sub, mode, qp, sh, L, invL, S.buf, C, k, lane, act,
+                                   lb_d2, lb_id, m);
         }
         __syncwarp();
         if (!stop && issued < nb) issue(issued);
@@ -1081,8 +1094,8 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
     }
     if (act && sub == 0 && !broken) {
       const int64_t row = order == 0 ? (int64_t)__float_as_int(qp.w) : (int64_t)(me.first + qi);
-      int32_t* oi = out_idx + row * k;
-      float* od = out_d2 + row * k;
+      int32_t* oi = out_idx + row * k_row + col0;
+      float* od = out_d2 + row * k_row + col0;
 #pragma unroll
       for (int e = 0; e < KMAX; ++e) {
         if (e >= KMAX - k) {
@@ -1125,16 +1138,16 @@ void n2n_knn_plane(const Layout& L, char* ws, int p, int k, float pl, cudaStream
       (int64_t)L.total, m); note_launch();
 }
 
-template <int KMAX, bool PER>
-void l2l_knn(const Layout& L, char* ws, int k, float pl, int order, int32_t* idx, float* d2,
-             cudaStream_t s) {
+template <int KMAX, bool PER, bool LB>
+void l2l_knn(const Layout& L, char* ws, int k, int k_row, int col0, int pass, float pl, int order,
+             int32_t* idx, float* d2, cudaStream_t s) {
   Meta* m = at<Meta>(ws, L.meta);
   const int sms = 152;
   const size_t smem = sizeof(L2LWarpSmem<KMAX>) * kL2LWarps;
-  cudaFuncSetAttribute(k_l2l_knn<KMAX, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_l2l_knn<KMAX, PER><<<sms * 8, 32 * kL2LWarps, smem, s>>>(
+  cudaFuncSetAttribute(k_l2l_knn<KMAX, PER, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_l2l_knn<KMAX, PER, LB><<<sms * 8, 32 * kL2LWarps, smem, s>>>(
       at<float4>(ws, L.pts), at<NodeRec>(ws, L.nodes[0]), at<uint2>(ws, L.ilo[0]),
-      at<IEntry>(ws, L.arena), k, pl, order, idx, d2, m); note_launch();
+      at<IEntry>(ws, L.arena), k, k_row, col0, kCtrWalk + pass, pl, order, idx, d2, m); note_launch();
 }
 
 template <bool PER>
@@ -1169,10 +1182,16 @@ void knn_all(const Layout& L, char* ws, float pl, int k, int order, int32_t* idx
     prof_end(kPhKnnSort, s);
   }
   prof_begin(kPhKnnL2L, s);
-  if (k <= 4) l2l_knn<4, PER>(L, ws, k, pl, order, idx, d2, s);
-  else if (k <= 8) l2l_knn<8, PER>(L, ws, k, pl, order, idx, d2, s);
-  else if (k <= 16) l2l_knn<16, PER>(L, ws, k, pl, order, idx, d2, s);
-  else l2l_knn<32, PER>(L, ws, k, pl, order, idx, d2, s);
+  if (k <= 4) l2l_knn<4, PER, false>(L, ws, k, k, 0, 0, pl, order, idx, d2, s);
+  else if (k <= 8) l2l_knn<8, PER, false>(L, ws, k, k, 0, 0, pl, order, idx, d2, s);
+  else if (k <= 16) l2l_knn<16, PER, false>(L, ws, k, k, 0, 0, pl, order, idx, d2, s);
+  else if (k <= kMaxK) l2l_knn<32, PER, false>(L, ws, k, k, 0, 0, pl, order, idx, d2, s);
+  else
+    for (int c0 = 0, pass = 0; c0 < k; c0 += kMaxK, ++pass) {  // k / 32 passes (at most 8 counters)
+      const int kp = k - c0 < kMaxK ? k - c0 : kMaxK;
+      if (c0 == 0) l2l_knn<32, PER, false>(L, ws, kp, k, c0, pass, pl, order, idx, d2, s);
+      else l2l_knn<32, PER, true>(L, ws, kp, k, c0, pass, pl, order, idx, d2, s);
+    }
   prof_end(kPhKnnL2L, s);
   k_walk_peak<<<1, 32, 0, s>>>(m); note_launch();
 }

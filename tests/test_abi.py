@@ -44,8 +44,9 @@ def test_workspace_bytes_grows_and_validates():
         with pytest.raises(jzt.JztError) as e:
             jzt.workspace_bytes(bad)
         assert e.value.code == jzt.JZT_ERR_INVALID
+    assert jzt.workspace_bytes(1000, 256) > jzt.workspace_bytes(1000, 32)
     with pytest.raises(jzt.JztError):
-        jzt.workspace_bytes(100, 33)
+        jzt.workspace_bytes(100, 257)
     for p in ({"nmax0": 33}, {"nmax0": -1}, {"plane_factor": 1}, {"heap_size": 17},
               {"alloc_fac_ilist": -1.0}):
         with pytest.raises(jzt.JztError) as e:
@@ -73,7 +74,7 @@ def test_synchronous_argument_errors():
     assert b"workspace too small" in lib.jzt_last_error()
     assert lib.jzt_tree_knn(None, 4, 0, vp(256), vp(256), None) == jzt.JZT_ERR_INVALID
     assert lib.jzt_tree_fof(None, 0.1, vp(256), None) == jzt.JZT_ERR_INVALID
-    assert lib.jzt_knn(vp(256), 100, 33, 0.0, vp(256), vp(256), vp(256), 1 << 20, None) == jzt.JZT_ERR_UNSUPPORTED
+    assert lib.jzt_knn(vp(256), 1000, 257, 0.0, vp(256), vp(256), vp(256), 1 << 20, None) == jzt.JZT_ERR_UNSUPPORTED
     assert lib.jzt_knn(vp(256), 10, 11, 0.0, vp(256), vp(256), vp(256), 1 << 20, None) == jzt.JZT_ERR_INVALID
     assert lib.jzt_knn(vp(256), 10, 0, 0.0, vp(256), vp(256), vp(256), 1 << 20, None) == jzt.JZT_ERR_INVALID
     assert lib.jzt_fof(vp(256), 10, 0.0, 0.0, vp(256), vp(256), 1 << 20, None) == jzt.JZT_ERR_INVALID

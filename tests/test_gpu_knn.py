@@ -5,6 +5,7 @@ import pytest
 
 import oracle
 import workloads
+from tests import parity
 from tests.gpu_util import knn_parity, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -116,3 +117,36 @@ def test_capacity_error_then_retry():
     assert st["required_bytes"] > tree.workspace.numel()
     tree = jzt.build(xt, periodic_L=1.0)
     knn_parity(tree, x, 16, 1.0)
+
+
+@pytest.mark.parametrize("k,L,gen", [(33, 1.0, "clustered"), (64, 0.0, "clustered"), (100, 1.0, "uniform"),
+                                     (256, 1.0, "clustered"), (97, 0.0, "uniform")])
+def test_k_above_32_passes(k, L, gen):
+    """k > 32 runs ceil(k/32) LeafToLeaf passes; rows equal the all-pairs oracle."""
+    import paper_2604_05885_gb300 as jzt
+    n = 5000
+    x = workloads.clustered(n, 70 + k, n_blobs=6) if gen == "clustered" else workloads.uniform(n, 70 + k)
+    tree = jzt.build(to_dev(x), periodic_L=L, workspace=jzt.alloc_workspace(n, k))
+    knn_parity(tree, x, k, L)
+
+
+def test_k_above_32_ties_across_pass_boundary():
+    """Lattice shells: the 32nd neighbour lies inside the 6-point shell at 2h, so the
+    tie at the pass boundary must continue in index order in the second pass."""
+    import paper_2604_05885_gb300 as jzt
+    xs = workloads.lattice(12, spacing_bits=4)
+    for k in (40, 64):
+        tree = jzt.build(to_dev(xs), periodic_L=1.0, workspace=jzt.alloc_workspace(len(xs), k))
+        idx, _ = knn_parity(tree, xs, k, 1.0)
+        ri, _ = oracle.knn_brute(xs, k, 1.0)
+        assert np.array_equal(idx, ri)
+
+
+def test_k_above_32_one_call_and_z_order():
+    import paper_2604_05885_gb300 as jzt
+    x = workloads.clustered(3000, 77, n_blobs=3)
+    idx, d2 = jzt.knn(to_dev(x), 70, 1.0)
+    ri, rd = oracle.knn_brute(x, 70, 1.0)
+    parity.check_knn(x, np.arange(len(x)), idx.cpu().numpy(), d2.cpu().numpy(), ri, rd, 1.0)
+    tree = jzt.build(to_dev(x), periodic_L=1.0, workspace=jzt.alloc_workspace(len(x), 70))
+    knn_parity(tree, x, 70, 1.0, order=1)
