@@ -59,6 +59,8 @@ def _load():
         lib.oracle_knn_brute.argtypes = [f32p, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                                          i64p, ctypes.c_int64, i32p, f64p, ctypes.c_int]
         lib.oracle_knn_cells.argtypes = lib.oracle_knn_brute.argtypes
+        lib.oracle_knn_brute_sets.argtypes = [f32p, ctypes.c_int64, f32p, ctypes.c_int64, ctypes.c_int,
+                                              ctypes.c_double, i32p, f64p, ctypes.c_int]
         lib.oracle_fof_brute.argtypes = [f32p, ctypes.c_int64, ctypes.c_double, ctypes.c_double, i32p]
         lib.oracle_fof_cells.argtypes = [f32p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, i32p, ctypes.c_int]
@@ -100,6 +102,21 @@ def _knn(fn, xyz, k, periodic_L, queries, threads):
 def knn_brute(xyz, k, periodic_L=0.0, queries=None, threads=0):
     """All-pairs exact kNN (Sec. III): rows ascending by (float64 d2, index), self included."""
     return _knn(_load().oracle_knn_brute, xyz, k, periodic_L, queries, threads)
+
+
+def knn_brute_sets(src, qry, k, periodic_L=0.0, threads=0):
+    """kNN of separate query points among source points (Sec. II-G): row r lists the
+    k sources nearest to query r, ascending by (float64 d2, source index)."""
+    s = np.ascontiguousarray(src, dtype=np.float32)
+    q = np.ascontiguousarray(qry, dtype=np.float32)
+    idx = np.empty((q.shape[0], k), dtype=np.int32)
+    d2 = np.empty((q.shape[0], k), dtype=np.float64)
+    rc = _load().oracle_knn_brute_sets(_ptr(s, ctypes.c_float), s.shape[0], _ptr(q, ctypes.c_float), q.shape[0],
+                                       int(k), float(periodic_L), _ptr(idx, ctypes.c_int32),
+                                       _ptr(d2, ctypes.c_double), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle kNN failed (rc={rc})")
+    return idx, d2
 
 
 def knn_cells(xyz, k, periodic_L=0.0, queries=None, threads=0):

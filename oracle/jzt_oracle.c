@@ -102,6 +102,25 @@ int oracle_knn_brute(const float *xyz, int64_t n, int k, double L,
     return 0;
 }
 
+/* kNN of separate query points among source points (Sec. II-G, multiple point
+ * types): for query r, the k source points with the smallest (d2, source index). */
+int oracle_knn_brute_sets(const float *src, int64_t n_src, const float *qry, int64_t n_qry, int k,
+                          double L, int32_t *out_idx, double *out_d2, int nthreads)
+{
+    if (n_src < 1 || k < 1 || k > n_src || n_qry < 0)
+        return -1;
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t r = 0; r < n_qry; ++r) {
+        double *kd = out_d2 + r * k;
+        int32_t *ki = out_idx + r * k;
+        int m = 0;
+        for (int64_t j = 0; j < n_src; ++j)
+            topk_insert(kd, ki, &m, k, pair_d2(qry + 3 * r, src + 3 * j, L), (int32_t)j);
+    }
+    return 0;
+}
+
 /* ---------------------------------------------------------------- union-find
  * Linking always points the larger root at the smaller one, so the root of
  * every set is its smallest member. */

@@ -376,3 +376,30 @@ def test_fof_rule():
     wrong[123] = 0 if lab[123] != 0 else 1
     with pytest.raises(AssertionError):
         parity.check_fof(wrong, s, lo)
+
+
+def test_knn_sets_pins():
+    """Query-vs-source oracle: against a full lexsort of the cross distance matrix,
+    against scipy's cKDTree on separate sets, equal to the self query when the
+    query set is the source set, and a query placed on a source point finds it first."""
+    rng = np.random.default_rng(41)
+    src = workloads.snap_unit(rng.random((700, 3)))
+    qry = workloads.snap_unit(rng.random((300, 3)))
+    for L in (0.0, 1.0):
+        ri, rd = oracle.knn_brute_sets(src, qry, 9, L)
+        d = qry[:, None, :].astype(np.float64) - src[None, :, :].astype(np.float64)
+        if L > 0:
+            d -= L * np.round(d / L)
+        d2 = (d * d).sum(-1)
+        order = np.lexsort((np.broadcast_to(np.arange(len(src)), d2.shape), d2), axis=1)[:, :9]
+        assert np.array_equal(ri, order)
+        assert np.allclose(rd, np.take_along_axis(d2, order, 1), rtol=0, atol=0)
+    from scipy.spatial import cKDTree
+    dd, ii = cKDTree(src.astype(np.float64)).query(qry.astype(np.float64), 5)
+    ri, rd = oracle.knn_brute_sets(src, qry, 5, 0.0)
+    assert np.allclose(np.sqrt(rd), dd) and np.array_equal(ri, ii)
+    si, sd = oracle.knn_brute(src, 7, 1.0)
+    qi, qd = oracle.knn_brute_sets(src, src, 7, 1.0)
+    assert np.array_equal(si, qi) and np.array_equal(sd, qd)
+    qi, qd = oracle.knn_brute_sets(src, src[[5, 17]], 1, 0.0)
+    assert list(qi[:, 0]) == [5, 17] and np.all(qd == 0.0)
