@@ -123,6 +123,26 @@ int jzt_tree_knn(jzt_tree *t, int k, int order, int32_t *d_idx, float *d_dist2, 
  * (Sec. IV-A).  Errors: JZT_ERR_INVALID (b <= 0 or not finite, periodic b >= L/2). */
 int jzt_tree_fof(jzt_tree *t, float b, int32_t *d_labels, void *stream);
 
+/* ---- Separate query and source points (Sec. II-G, multiple point types).
+ * One tree is built jointly over the n_src source points followed by the n_qry
+ * query points (one combined index for the sort; a node splits while it holds
+ * more than N_max^(p) points of both types together, which bounds each type's
+ * count as Sec. II-G requires).  After the build the sorted points are separated
+ * by type, each in z order, and every leaf gets a source range and a query
+ * range; node counts used by the radius search are source counts.
+ * jzt_tree_knn on such a tree writes n_qry rows (row r: query r; order 1: query
+ * z order) of the k nearest sources (source indices), 1 <= k <= min(256, n_src);
+ * jzt_tree_fof returns JZT_ERR_UNSUPPORTED.  Workspace: jzt_workspace_bytes_query.
+ * Errors as jzt_build, plus JZT_ERR_INVALID for n_src < 1 or n_qry < 1. */
+int jzt_workspace_bytes_query(int64_t n_src, int64_t n_qry, int k, const jzt_params *p, size_t *bytes);
+int jzt_build_query(const float *d_src, int64_t n_src, const float *d_qry, int64_t n_qry,
+                    float periodic_L, const jzt_params *p, void *d_ws, size_t ws_bytes,
+                    void *stream, jzt_tree **out);
+/* One call: build over both sets, then kNN of every query point among the sources. */
+int jzt_knn_query(const float *d_src, int64_t n_src, const float *d_qry, int64_t n_qry, int k,
+                  float periodic_L, int32_t *d_idx, float *d_dist2, void *d_ws, size_t ws_bytes,
+                  void *stream);
+
 /* One-call forms: build, then walk, on the same workspace. */
 int jzt_knn(const float *d_xyz, int64_t n, int k, float periodic_L,
             int32_t *d_idx, float *d_dist2, void *d_ws, size_t ws_bytes, void *stream);

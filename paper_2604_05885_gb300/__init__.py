@@ -41,7 +41,8 @@ _NAMES = {0: "ok", -1: "invalid", -2: "unsupported", -3: "cuda", -4: "workspace"
 SYMBOLS = ("jzt_workspace_bytes", "jzt_build", "jzt_tree_knn", "jzt_tree_fof", "jzt_knn", "jzt_fof",
            "jzt_status", "jzt_tree_arrays", "jzt_tree_plane", "jzt_tree_free", "jzt_last_error",
            "jzt_version", "jzt_profile_enable", "jzt_profile_read", "jzt_profile_phase_name",
-           "jzt_knn_noalloc", "jzt_batch_run")
+           "jzt_knn_noalloc", "jzt_batch_run", "jzt_workspace_bytes_query", "jzt_build_query",
+           "jzt_knn_query")
 JZT_OP_KNN = 0
 JZT_OP_FOF = 1
 
@@ -104,6 +105,11 @@ def _load():
     lib.jzt_batch_run.argtypes = [ctypes.POINTER(Job), ctypes.c_int, ctypes.POINTER(Params),
                                   ctypes.POINTER(vp), ctypes.POINTER(sz), ctypes.POINTER(vp), ctypes.c_int, vp, vp]
     lib.jzt_batch_run.restype = ctypes.c_int
+    lib.jzt_workspace_bytes_query.argtypes = [i64, i64, ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(sz)]
+    lib.jzt_build_query.argtypes = [vp, i64, vp, i64, f32, ctypes.POINTER(Params), vp, sz, vp, ctypes.POINTER(vp)]
+    lib.jzt_knn_query.argtypes = [vp, i64, vp, i64, ctypes.c_int, f32, vp, vp, vp, sz, vp]
+    for name in ("jzt_workspace_bytes_query", "jzt_build_query", "jzt_knn_query"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.jzt_tree_free.argtypes = [vp]
     lib.jzt_tree_free.restype = None
     lib.jzt_last_error.restype = ctypes.c_char_p
@@ -209,6 +215,7 @@ class Tree:
         _check_xyz(xyz)
         n = xyz.shape[0]
         self.n = n
+        self.n_rows = n
         self.periodic_L = float(periodic_L)
         self.params = params
         self.workspace = workspace if workspace is not None else alloc_workspace(
@@ -221,8 +228,8 @@ class Tree:
     def knn(self, k: int, order: int = 0, out=None, stream=None):
         dev = self.workspace.device
         if out is None:
-            idx = torch.empty((self.n, k), dtype=torch.int32, device=dev)
-            d2 = torch.empty((self.n, k), dtype=torch.float32, device=dev)
+            idx = torch.empty((self.n_rows, k), dtype=torch.int32, device=dev)
+            d2 = torch.empty((self.n_rows, k), dtype=torch.float32, device=dev)
         else:
             idx, d2 = out
         _check(lib.jzt_tree_knn(self._h, int(k), int(order), ctypes.c_void_p(idx.data_ptr()),
@@ -269,6 +276,58 @@ class Tree:
         if h is not None and h.value:
             lib.jzt_tree_free(h)
             self._h = ctypes.c_void_p(0)
+
+
+def workspace_bytes_query(n_src: int, n_qry: int, k: int = 0, params=None) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib.jzt_workspace_bytes_query(int(n_src), int(n_qry), int(k), _params(params), ctypes.byref(out)))
+    return int(out.value)
+
+
+class QueryTree(Tree):
+    """A tree over source points and separate query points (jzt_build_query):
+    knn(k) returns one row per query point listing source indices."""
+
+    def __init__(self, src: torch.Tensor, qry: torch.Tensor, periodic_L: float = 0.0, params=None,
+                 workspace: torch.Tensor | None = None, stream=None, k_max: int = 32):
+        _check_xyz(src)
+        _check_xyz(qry)
+        self.n = src.shape[0] + qry.shape[0]
+        self.n_src = src.shape[0]
+        self.n_rows = qry.shape[0]
+        self.periodic_L = float(periodic_L)
+        self.params = params
+        self.workspace = workspace if workspace is not None else torch.empty(
+            workspace_bytes_query(self.n_src, self.n_rows, min(int(k_max), self.n_src, 256), params),
+            dtype=torch.uint8, device=src.device)
+        self._h = ctypes.c_void_p(0)
+        _check(lib.jzt_build_query(ctypes.c_void_p(src.data_ptr()), self.n_src, ctypes.c_void_p(qry.data_ptr()),
+                                   self.n_rows, self.periodic_L, _params(params),
+                                   ctypes.c_void_p(self.workspace.data_ptr()), self.workspace.numel(),
+                                   ctypes.c_void_p(_stream(stream)), ctypes.byref(self._h)))
+
+
+def build_query(src, qry, periodic_L=0.0, params=None, workspace=None, stream=None, k_max=32) -> QueryTree:
+    return QueryTree(src, qry, periodic_L, params, workspace, stream, k_max)
+
+
+def knn_query(src: torch.Tensor, qry: torch.Tensor, k: int, periodic_L: float = 0.0, workspace=None, stream=None,
+              check=True):
+    """One-call kNN of query points among source points (jzt_knn_query); returns
+    (idx [N_qry, k] int32 source indices, dist2 [N_qry, k] float32)."""
+    _check_xyz(src)
+    _check_xyz(qry)
+    ns, nq = src.shape[0], qry.shape[0]
+    ws = workspace if workspace is not None else torch.empty(workspace_bytes_query(ns, nq, min(k, ns)),
+                                                             dtype=torch.uint8, device=src.device)
+    idx = torch.empty((nq, k), dtype=torch.int32, device=src.device)
+    d2 = torch.empty((nq, k), dtype=torch.float32, device=src.device)
+    _check(lib.jzt_knn_query(ctypes.c_void_p(src.data_ptr()), ns, ctypes.c_void_p(qry.data_ptr()), nq, int(k),
+                             float(periodic_L), ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
+                             ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(_stream(stream))))
+    if check:
+        status(ws, stream, raise_on_error=True)
+    return idx, d2
 
 
 def build(xyz, periodic_L=0.0, params=None, workspace=None, stream=None, k_max=32) -> Tree:

@@ -75,10 +75,11 @@ int num_planes(int64_t n, const Params& P) {
 
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* Lp) {
+int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* Lp, int64_t n_src) {
   Layout L;
   std::memset(&L, 0, sizeof(L));
   L.n = n;
+  L.n_src = (n_src >= 0 && n_src < n) ? n_src : n;
   L.nmax0 = P.nmax0;
   L.c = P.c;
   L.n_target = P.n_target;
@@ -128,6 +129,12 @@ int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* L
   for (int p = 0; p < L.n_planes; ++p) L.lk[p] = take((size_t)L.cap_nodes[p]);
   L.ig_pt = take(4 * (size_t)n);
   L.minorig = take(4 * (size_t)n);
+  if (L.n_src < n) {
+    L.pts2 = take(16 * (size_t)n);
+    L.src_pos = take(4 * (size_t)(n + 1));
+    L.qrange = take(8 * (size_t)L.cap_nodes[0]);
+    L.tile_cnt = take(4 * (size_t)(scan_tiles + 1));
+  }
   // Interaction-list arena (Eq. alloc_ilist): fac * N / (N_max^(0)/2) entries,
   // scaled by k/16 for k > 16, plus the dense super-node list; last in the
   // workspace so that a larger workspace simply grows it.
@@ -154,7 +161,8 @@ using namespace jzt;
 struct jzt_tree {
   Layout L;
   char* ws;
-  int64_t n;
+  int64_t n;      // all points
+  int64_t n_src;  // source points (== n for one point set)
   float periodic_L;
 };
 
@@ -216,6 +224,59 @@ int jzt_build(const float* d_xyz, int64_t n, float periodic_L, const jzt_params*
   t->L = L;
   t->ws = static_cast<char*>(d_ws);
   t->n = n;
+  t->n_src = n;
+  t->periodic_L = periodic_L > 0.0f ? periodic_L : 0.0f;
+  *out = t;
+  return JZT_OK;
+}
+
+int jzt_workspace_bytes_query(int64_t n_src, int64_t n_qry, int k, const jzt_params* p, size_t* bytes) {
+  if (!bytes) return fail(JZT_ERR_INVALID, "bytes is null");
+  if (n_src < 1 || n_qry < 1) return fail(JZT_ERR_INVALID, "need at least one source and one query point");
+  if (int e = check_n(n_src + n_qry)) return e;
+  if (k < 0 || k > kMaxKTotal) return fail(JZT_ERR_INVALID, "k must be in 0..256");
+  Params P;
+  const char* why = nullptr;
+  if (int e = resolve_params(p, &P, &why)) return fail(e, why);
+  Layout L;
+  compute_layout(n_src + n_qry, P, k, 0, &L, n_src);
+  *bytes = L.total;
+  return JZT_OK;
+}
+
+int jzt_build_query(const float* d_src, int64_t n_src, const float* d_qry, int64_t n_qry, float periodic_L,
+                    const jzt_params* p, void* d_ws, size_t ws_bytes, void* stream, jzt_tree** out) {
+  if (!out) return fail(JZT_ERR_INVALID, "out is null");
+  *out = nullptr;
+  if (!d_src || !d_qry || !d_ws) return fail(JZT_ERR_INVALID, "null device pointer");
+  if ((reinterpret_cast<uintptr_t>(d_src) & 3u) || (reinterpret_cast<uintptr_t>(d_qry) & 3u))
+    return fail(JZT_ERR_INVALID, "point arrays must be 4-byte aligned");
+  if (reinterpret_cast<uintptr_t>(d_ws) & 255u) return fail(JZT_ERR_INVALID, "d_ws must be 256-byte aligned");
+  if (n_src < 1 || n_qry < 1) return fail(JZT_ERR_INVALID, "need at least one source and one query point");
+  if (int e = check_n(n_src + n_qry)) return e;
+  if (int e = check_L(periodic_L)) return e;
+  Params P;
+  const char* why = nullptr;
+  if (int e = resolve_params(p, &P, &why)) return fail(e, why);
+  const int64_t n = n_src + n_qry;
+  Layout L;
+  compute_layout(n, P, 0, ws_bytes, &L, n_src);
+  if (L.cap_ilist < 0) {
+    Layout need;
+    compute_layout(n, P, 0, 0, &need, n_src);
+    return fail(JZT_ERR_WORKSPACE, "workspace too small: need " + std::to_string(need.total) +
+                                       " bytes, got " + std::to_string(ws_bytes));
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  launch_build_sets(d_src, n_src, d_qry, n_qry, periodic_L > 0.0f ? periodic_L : 0.0f, L, static_cast<char*>(d_ws),
+                    s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "jzt_build_query launch");
+  jzt_tree* t = new jzt_tree;
+  t->L = L;
+  t->ws = static_cast<char*>(d_ws);
+  t->n = n;
+  t->n_src = n_src;
   t->periodic_L = periodic_L > 0.0f ? periodic_L : 0.0f;
   *out = t;
   return JZT_OK;
@@ -224,7 +285,7 @@ int jzt_build(const float* d_xyz, int64_t n, float periodic_L, const jzt_params*
 int jzt_tree_knn(jzt_tree* t, int k, int order, int32_t* d_idx, float* d_dist2, void* stream) {
   if (!t) return fail(JZT_ERR_INVALID, "tree is null");
   if (!d_idx || !d_dist2) return fail(JZT_ERR_INVALID, "null output pointer");
-  if (k < 1 || (int64_t)k > t->n) return fail(JZT_ERR_INVALID, "k must satisfy 1 <= k <= N");
+  if (k < 1 || (int64_t)k > t->n_src) return fail(JZT_ERR_INVALID, "k must satisfy 1 <= k <= N (sources)");
   if (k > kMaxKTotal) return fail(JZT_ERR_UNSUPPORTED, "k > 256 is not supported");
   if (order != 0 && order != 1) return fail(JZT_ERR_INVALID, "order must be 0 (input) or 1 (z)");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -236,6 +297,7 @@ int jzt_tree_knn(jzt_tree* t, int k, int order, int32_t* d_idx, float* d_dist2, 
 
 int jzt_tree_fof(jzt_tree* t, float b, int32_t* d_labels, void* stream) {
   if (!t) return fail(JZT_ERR_INVALID, "tree is null");
+  if (t->n_src < t->n) return fail(JZT_ERR_UNSUPPORTED, "FoF runs on a tree of one point set");
   if (!d_labels) return fail(JZT_ERR_INVALID, "null output pointer");
   if (!(b > 0.0f) || std::isinf(b)) return fail(JZT_ERR_INVALID, "b must be positive and finite");
   if (t->periodic_L > 0.0f && !(b < 0.5f * t->periodic_L))
@@ -256,6 +318,20 @@ int jzt_knn(const float* d_xyz, int64_t n, int k, float periodic_L, int32_t* d_i
   if (!d_idx || !d_dist2) return fail(JZT_ERR_INVALID, "null output pointer");
   jzt_tree* t = nullptr;
   if (int e = jzt_build(d_xyz, n, periodic_L, nullptr, d_ws, ws_bytes, stream, &t)) return e;
+  int e = jzt_tree_knn(t, k, 0, d_idx, d_dist2, stream);
+  jzt_tree_free(t);
+  return e;
+}
+
+int jzt_knn_query(const float* d_src, int64_t n_src, const float* d_qry, int64_t n_qry, int k, float periodic_L,
+                  int32_t* d_idx, float* d_dist2, void* d_ws, size_t ws_bytes, void* stream) {
+  if (k < 1 || k > kMaxKTotal || (int64_t)k > n_src) {
+    if (k > kMaxKTotal && (int64_t)k <= n_src) return fail(JZT_ERR_UNSUPPORTED, "k > 256 is not supported");
+    return fail(JZT_ERR_INVALID, "k must satisfy 1 <= k <= N (sources)");
+  }
+  if (!d_idx || !d_dist2) return fail(JZT_ERR_INVALID, "null output pointer");
+  jzt_tree* t = nullptr;
+  if (int e = jzt_build_query(d_src, n_src, d_qry, n_qry, periodic_L, nullptr, d_ws, ws_bytes, stream, &t)) return e;
   int e = jzt_tree_knn(t, k, 0, d_idx, d_dist2, stream);
   jzt_tree_free(t);
   return e;

@@ -486,14 +486,124 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const uint64_t* __
 }
 
 // ------------------------------------------------------------------ gather
-__global__ void k_gather(const float* __restrict__ xyz, const uint32_t* __restrict__ perm, int64_t n,
-                         float4* __restrict__ pts) {
+// Combined index p < n1 reads xyz[p], otherwise xyz2[p - n1] (two point sets).
+__global__ void k_gather(const float* __restrict__ xyz, const float* __restrict__ xyz2, int64_t n1,
+                         const uint32_t* __restrict__ perm, int64_t n, float4* __restrict__ pts) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     uint32_t p = perm[i];
     if (p >= (uint64_t)n) p = 0;  // only after a failed sort (status already set)
-    const float* s = xyz + 3 * (int64_t)p;
+    const float* s = (int64_t)p < n1 ? xyz + 3 * (int64_t)p : xyz2 + 3 * ((int64_t)p - n1);
     pts[i] = make_float4(__ldg(s), __ldg(s + 1), __ldg(s + 2), __uint_as_float(p));
+  }
+}
+
+// ---------------------------------------------------------------- two point sets
+// Sorted positions are split by type, stably: sources keep their z order in
+// pts2[0, n_src), queries in pts2[n_src, n) (Sec. II-G).  src_pos[i] = number
+// of sources before sorted position i (src_pos[n] = n_src).
+constexpr int kTypeThreads = 256;
+constexpr int kTypePer = kScanTile / kTypeThreads;
+
+__global__ void __launch_bounds__(kTypeThreads) k_src_tile_counts(const float4* __restrict__ pts, int64_t n,
+                                                                  int64_t n_src, int32_t* tile_cnt) {
+  __shared__ int32_t red[kTypeThreads / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int c = 0;
+#pragma unroll
+  for (int e = 0; e < kTypePer; ++e) {
+    const int64_t i = base + e * kTypeThreads + threadIdx.x;
+    if (i < n) c += (int64_t)__float_as_uint(pts[i].w) < n_src ? 1 : 0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane_id() == 0) red[warp_id()] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kTypeThreads / 32; ++w) t += red[w];
+    tile_cnt[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the tile counts in place (one block; tiles <= 2^20).
+__global__ void __launch_bounds__(1024) k_scan_tile_counts(int32_t* tile_cnt, int64_t n_tiles) {
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t b = 0; b < n_tiles; b += 1024) {
+    const int64_t i = b + threadIdx.x;
+    const uint32_t v = i < n_tiles ? (uint32_t)tile_cnt[i] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_excl_scan<1024>(v, &total);
+    if (i < n_tiles) tile_cnt[i] = carry + (int32_t)ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += (int32_t)total;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kTypeThreads) k_split_types(const float4* __restrict__ pts, int64_t n,
+                                                              int64_t n_src, const int32_t* __restrict__ tile_off,
+                                                              float4* __restrict__ pts2, int32_t* __restrict__ src_pos) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kTypePer;  // blocked items
+  float4 v[kTypePer];
+  int c = 0;
+#pragma unroll
+  for (int e = 0; e < kTypePer; ++e) {
+    const int64_t i = base + e;
+    v[e] = i < n ? pts[i] : make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
+    c += (i < n && (int64_t)__float_as_uint(v[e].w) < n_src) ? 1 : 0;
+  }
+  uint32_t total;
+  int32_t r = tile_off[blockIdx.x] + (int32_t)block_excl_scan<kTypeThreads>((uint32_t)c, &total);
+#pragma unroll
+  for (int e = 0; e < kTypePer; ++e) {
+    const int64_t i = base + e;
+    if (i >= n) break;
+    src_pos[i] = r;
+    const int64_t orig = (int64_t)__float_as_uint(v[e].w);
+    if (orig < n_src) {
+      pts2[r] = v[e];
+      ++r;
+    } else {
+      pts2[n_src + (i - r)] = make_float4(v[e].x, v[e].y, v[e].z, __uint_as_float((uint32_t)(orig - n_src)));
+    }
+  }
+  if (base <= n - 1 && n - 1 < base + kTypePer) src_pos[n] = (int32_t)n_src;
+}
+
+// Leaves: (first, count) become the source range in pts2; qrange = query range
+// in the query part pts2 + n_src.  Boxes stay those of all points (conservative
+// for either type).
+__global__ void k_leaf_types(NodeRec* __restrict__ leaves, const int32_t* __restrict__ src_pos,
+                             uint2* __restrict__ qrange, const Meta* m) {
+  if (warp_failed(m)) return;
+  const int64_t nl = m->n_nodes[0];
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < nl; l += (int64_t)gridDim.x * blockDim.x) {
+    NodeRec r = leaves[l];
+    const int32_t s0 = src_pos[r.first], s1 = src_pos[r.first + r.count];
+    qrange[l] = make_uint2((uint32_t)(r.first - s0), (uint32_t)(r.count - (s1 - s0)));
+    r.first = s0;
+    r.count = s1 - s0;
+    leaves[l] = r;
+  }
+}
+
+// Upper nodes: count = sum of the children's (source) counts.
+__global__ void k_upper_counts(const int32_t* __restrict__ spl, const NodeRec* __restrict__ child,
+                               NodeRec* __restrict__ nodes, int plane, const Meta* m) {
+  if (warp_failed(m)) return;
+  const int64_t nn = m->n_nodes[plane];
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = lane_id();
+  for (int64_t P = gw; P < nn; P += nw) {
+    int c = 0;
+    for (int64_t ch = spl[P] + lane; ch < spl[P + 1]; ch += 32) c += child[ch].count;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) nodes[P].count = c;
   }
 }
 
@@ -806,17 +916,37 @@ void launch_super_level(const Layout& L, char* ws, cudaStream_t s) {
       at<int32_t>(ws, L.spl[P]), P - 1, L.ngr, L.cap_nodes[P], m); note_launch();
 }
 
-void launch_build(const float* d_xyz, int64_t n, float periodic_L, const Layout& L, char* ws,
-                  cudaStream_t s) {
+namespace {
+
+void bbox_part(const float* d, int64_t n, float periodic_L, Meta* m, cudaStream_t s) {
+  const bool vec = (reinterpret_cast<uintptr_t>(d) & 15u) == 0;
+  const int gb = grid_for((n + 3) / 4, 256, 152 * 8);
+  if (vec) k_bbox<true><<<gb, 256, 0, s>>>(d, n, periodic_L, m);
+  else k_bbox<false><<<gb, 256, 0, s>>>(d, n, periodic_L, m);
+  note_launch();
+}
+
+void keygen_part(const float* d, int64_t n, Meta* m, uint64_t* keys, cudaStream_t s) {
+  // the vectorised path loads float4 groups of points and stores key pairs as
+  // 16-byte words: both addresses must be 16-byte aligned (the query part of a
+  // two-set build starts at keys + n_src)
+  const bool vec = (reinterpret_cast<uintptr_t>(d) & 15u) == 0 && (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+  const int gb = grid_for((n + 3) / 4, 256, 152 * 8);
+  if (vec) k_keygen<true><<<gb, 256, 0, s>>>(d, n, m, keys);
+  else k_keygen<false><<<gb, 256, 0, s>>>(d, n, m, keys);
+  note_launch();
+}
+
+// Points a (n_a) then b (n_b; may be null with n_b = 0) under one combined index.
+void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, float periodic_L,
+                const Layout& L, char* ws, cudaStream_t s) {
+  const int64_t n = n_a + n_b;
   Meta* m = at<Meta>(ws, L.meta);
   const int sms = 152;
   prof_begin(kPhBox, s);
   k_init_meta<<<1, 256, 0, s>>>(m, L.n_planes); note_launch();
-  const bool vec = (reinterpret_cast<uintptr_t>(d_xyz) & 15u) == 0;
-  const int gb = grid_for((n + 3) / 4, 256, sms * 8);
-  if (vec) k_bbox<true><<<gb, 256, 0, s>>>(d_xyz, n, periodic_L, m);
-  else k_bbox<false><<<gb, 256, 0, s>>>(d_xyz, n, periodic_L, m);
-  note_launch();
+  bbox_part(d_a, n_a, periodic_L, m, s);
+  if (n_b > 0) bbox_part(d_b, n_b, periodic_L, m, s);
   k_finish_box<<<1, 32, 0, s>>>(m, periodic_L); note_launch();
   prof_end(kPhBox, s);
   prof_begin(kPhKeys, s);
@@ -824,9 +954,8 @@ void launch_build(const float* d_xyz, int64_t n, float periodic_L, const Layout&
   uint64_t* keys_b = at<uint64_t>(ws, L.keys_b);
   uint32_t* vals_a = at<uint32_t>(ws, L.vals_a);
   uint32_t* vals_b = at<uint32_t>(ws, L.vals_b);
-  if (vec) k_keygen<true><<<gb, 256, 0, s>>>(d_xyz, n, m, keys_a);
-  else k_keygen<false><<<gb, 256, 0, s>>>(d_xyz, n, m, keys_a);
-  note_launch();
+  keygen_part(d_a, n_a, m, keys_a, s);
+  if (n_b > 0) keygen_part(d_b, n_b, m, keys_a + n_a, s);
   k_radix_offsets<<<1, 32 * kRadixPasses, 0, s>>>(m); note_launch();
   // look-back tables of all passes, zeroed once
   uint32_t* lookback = at<uint32_t>(ws, L.lookback);
@@ -854,7 +983,7 @@ void launch_build(const float* d_xyz, int64_t n, float periodic_L, const Layout&
   prof_end(kPhSort, s);
   prof_begin(kPhGather, s);
   float4* pts = at<float4>(ws, L.pts);
-  k_gather<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(d_xyz, vals_a, n, pts); note_launch();
+  k_gather<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(d_a, d_b, n_a, vals_a, n, pts); note_launch();
 
   prof_end(kPhGather, s);
   prof_begin(kPhSplits, s);
@@ -886,7 +1015,34 @@ void launch_build(const float* d_xyz, int64_t n, float periodic_L, const Layout&
     k_upper_nodes<<<grid_for(L.cap_nodes[p] * 32, 256, sms * 16), 256, 0, s>>>(
         at<int32_t>(ws, L.spl[p]), at<int32_t>(ws, L.gap[p]), at<NodeRec>(ws, L.nodes[p - 1]),
         at<NodeRec>(ws, L.nodes[p]), p, m); note_launch();
+  if (n_b > 0) {
+    // split the sorted points by type; leaves get source ranges and query ranges,
+    // node counts become source counts
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    int32_t* tile_cnt = at<int32_t>(ws, L.tile_cnt);
+    k_src_tile_counts<<<(unsigned)tiles, kTypeThreads, 0, s>>>(pts, n, n_a, tile_cnt); note_launch();
+    k_scan_tile_counts<<<1, 1024, 0, s>>>(tile_cnt, tiles); note_launch();
+    k_split_types<<<(unsigned)tiles, kTypeThreads, 0, s>>>(pts, n, n_a, tile_cnt, at<float4>(ws, L.pts2),
+                                                             at<int32_t>(ws, L.src_pos)); note_launch();
+    k_leaf_types<<<grid_for(L.cap_nodes[0], 256, sms * 8), 256, 0, s>>>(
+        at<NodeRec>(ws, L.nodes[0]), at<int32_t>(ws, L.src_pos), at<uint2>(ws, L.qrange), m); note_launch();
+    for (int p = 1; p < L.n_planes; ++p)
+      k_upper_counts<<<grid_for(L.cap_nodes[p] * 32, 256, sms * 16), 256, 0, s>>>(
+          at<int32_t>(ws, L.spl[p]), at<NodeRec>(ws, L.nodes[p - 1]), at<NodeRec>(ws, L.nodes[p]), p, m);
+    note_launch(L.n_planes - 1);
+  }
   prof_end(kPhNodes, s);
+}
+
+}  // namespace
+
+void launch_build(const float* d_xyz, int64_t n, float periodic_L, const Layout& L, char* ws, cudaStream_t s) {
+  build_impl(d_xyz, n, nullptr, 0, periodic_L, L, ws, s);
+}
+
+void launch_build_sets(const float* d_src, int64_t n_src, const float* d_qry, int64_t n_qry, float periodic_L,
+                       const Layout& L, char* ws, cudaStream_t s) {
+  build_impl(d_src, n_src, d_qry, n_qry, periodic_L, L, ws, s);
 }
 
 }  // namespace jzt

@@ -87,6 +87,13 @@ struct Layout {
   size_t lk[kMaxPlanes];        // FoF: uint8 linked flag per node
   size_t ig_pt;                 // FoF: int32 group pointer per sorted point
   size_t minorig;               // FoF: int32 smallest original index per root
+  // two point sets (source points first, then query points; Sec. II-G): n_src
+  // sources, n - n_src queries; n_src == n for one set
+  int64_t n_src;
+  size_t pts2;                  // float4 [n]: sources (z order), then queries (z order)
+  size_t src_pos;               // int32 [n + 1]: sources before each sorted position
+  size_t qrange;                // uint2 per leaf: (first query in the query part, count)
+  size_t tile_cnt;              // int32 per scan tile: sources in the tile, then offsets
   size_t total;
 };
 
@@ -115,7 +122,8 @@ int resolve_params(const jzt_params* p, Params* out, const char** why);
 int num_planes(int64_t n, const Params& P);
 // ws_bytes == 0: size the interaction-list arena for k (jzt_workspace_bytes);
 // otherwise the arena takes the whole remainder of a ws_bytes workspace.
-int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* L);
+// n_src in [0, n): a tree over n_src source points followed by n - n_src query points.
+int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* L, int64_t n_src = -1);
 
 // ---------------------------------------------------------------- instrumentation (prof.cu)
 enum Phase : int {
@@ -134,6 +142,11 @@ int profile_read(double* ms, int64_t* counts, int n, long long* launches);
 // build_tree.cu
 void launch_build(const float* d_xyz, int64_t n, float periodic_L, const Layout& L,
                   char* ws, cudaStream_t s);
+// two point sets: the tree is built over sources then queries (combined index),
+// then the sorted points are split by type (sources first) and the leaves get
+// per-type ranges; node counts become source counts (Sec. II-G)
+void launch_build_sets(const float* d_src, int64_t n_src, const float* d_qry, int64_t n_qry, float periodic_L,
+                       const Layout& L, char* ws, cudaStream_t s);
 // walk_knn.cu
 void launch_knn(const Layout& L, char* ws, float periodic_L, int k, int order, int32_t* d_idx,
                 float* d_d2, cudaStream_t s);

@@ -920,6 +920,8 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
                                                            const uint2* __restrict__ ilo,
                                                            const IEntry* __restrict__ arena, int k,
                                                            int k_row, int col0, int ctr,
+                                                           const float4* __restrict__ qpts,
+                                                           const uint2* __restrict__ qrange,
                                                            float L, int order,
                                                            int32_t* __restrict__ out_idx,
                                                            float* __restrict__ out_d2, Meta* m) {
@@ -942,12 +944,20 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
     leaf = __shfl_sync(kFull, leaf, 0);
     if (leaf >= nl) break;
     const NodeRec me = leaves[leaf];
-    const int q = me.count;
+    // query points of the leaf: the leaf's own points, or (two point sets) its
+    // query range; sources are staged from pts by the listed leaves' ranges
+    int q = me.count, qfirst = me.first;
+    if (qrange) {
+      const uint2 qr = qrange[leaf];
+      qfirst = (int)qr.x;
+      q = (int)qr.y;
+    }
+    if (q == 0) continue;
     int G = 1;
     while (G < 32 && 2 * G * q <= 32) G *= 2;
     const int qi = lane / G, sub = lane & (G - 1);
     const bool act = qi < q;
-    const float4 qp = act ? pts[me.first + qi] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 qp = act ? qpts[qfirst + qi] : make_float4(0.f, 0.f, 0.f, 0.f);
     Cand<KMAX> C;
     C.F.init(k, -INFINITY, INFINITY);
     C.nb = C.nm = 0;
@@ -956,7 +966,7 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
     float lb_d2 = -INFINITY;  // lower bound key (previous pass's last), LB only
     int lb_id = -1;
     if (LB && act) {
-      const int64_t row = order == 0 ? (int64_t)__float_as_int(qp.w) : (int64_t)(me.first + qi);
+      const int64_t row = order == 0 ? (int64_t)__float_as_int(qp.w) : (int64_t)(qfirst + qi);
       lb_d2 = out_d2[row * k_row + col0 - 1];
       lb_id = out_idx[row * k_row + col0 - 1];
     }
@@ -1005,7 +1015,7 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
         const int cnt = __float_as_int(S.meta[e][2].w) & 0xff;
         const int st = e % kStages;
         __syncwarp();
-        if (lane == 0) {
+        if (lane == 0 && cnt > 0) {  // a source leaf without sources (two point sets) has no copy
           fence_proxy_async();
           mbar_expect_tx(&S.bar[st], (uint32_t)cnt * 16u);
           bulk_g2s(&S.pts[st][0], pts + first, (uint32_t)cnt * 16u, &S.bar[st]);
@@ -1016,29 +1026,33 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
       while (done < issued) {
         const uint32_t e = done;
         const int st = e % kStages;
-        const bool landed = __all_sync(kFull, mbar_wait(&S.bar[st], (parity >> st) & 1u));
-        if (!landed) {
-          if (lane == 0) set_error(m, JZT_ERR_TIMEOUT, kStageLeaf);
-          broken = true;
-          // give the copies still in flight a bounded chance to land before leaving
-          for (uint32_t r = done + 1; r < issued; ++r) {
-            const int s2 = r % kStages;
-            (void)__all_sync(kFull, mbar_wait(&S.bar[s2], (parity >> s2) & 1u));
-          }
-          break;
-        }
-        parity ^= 1u << st;
-        ++done;
-        ++st_examined;
         const float4 m0 = S.meta[e][0], m1 = S.meta[e][1], m2 = S.meta[e][2];
         const int cnt = __float_as_int(m2.w) & 0xff;
         const int mode = __float_as_int(m2.w) >> 8;
-        // pad the stage with NaN points (their distances fail every test)
-        if (lane >= cnt) S.pts[st][lane] = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff),
-                                                       __int_as_float(0x7fffffff), __int_as_float(INT_MAX));
+        if (cnt > 0) {
+          const bool landed = __all_sync(kFull, mbar_wait(&S.bar[st], (parity >> st) & 1u));
+          if (!landed) {
+            if (lane == 0) set_error(m, JZT_ERR_TIMEOUT, kStageLeaf);
+            broken = true;
+            // give the copies still in flight a bounded chance to land before leaving
+            for (uint32_t r = done + 1; r < issued; ++r) {
+              const int s2 = r % kStages;
+              if ((__float_as_int(S.meta[r][2].w) & 0xff) > 0)
+                (void)__all_sync(kFull, mbar_wait(&S.bar[s2], (parity >> s2) & 1u));
+            }
+            break;
+          }
+          parity ^= 1u << st;
+          // pad the stage with NaN points (their distances fail every test)
+          if (lane >= cnt) S.pts[st][lane] = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff),
+                                                         __int_as_float(0x7fffffff), __int_as_float(INT_MAX));
+        }
+        ++done;
+        ++st_examined;
         __syncwarp();
         bool skip = !__any_sync(kFull, act && m0.w <= C.thr);
-        if (skip && sorted) stop = true;
+        if (skip && sorted) stop = true;  // r_low only grows along a sorted list
+        skip = skip || cnt == 0;          // a leaf without sources is passed over, not a stop
         const float sh[3] = {m2.x, m2.y, m2.z};
         if (!skip) {
           // point-to-box lower bound against this lane's threshold, in the image
@@ -1093,7 +1107,7 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
       if (lane == 0) atomicAdd(&m->knn_stats[2], a);
     }
     if (act && sub == 0 && !broken) {
-      const int64_t row = order == 0 ? (int64_t)__float_as_int(qp.w) : (int64_t)(me.first + qi);
+      const int64_t row = order == 0 ? (int64_t)__float_as_int(qp.w) : (int64_t)(qfirst + qi);
       int32_t* oi = out_idx + row * k_row + col0;
       float* od = out_d2 + row * k_row + col0;
 #pragma unroll
@@ -1145,9 +1159,14 @@ void l2l_knn(const Layout& L, char* ws, int k, int k_row, int col0, int pass, fl
   const int sms = 152;
   const size_t smem = sizeof(L2LWarpSmem<KMAX>) * kL2LWarps;
   cudaFuncSetAttribute(k_l2l_knn<KMAX, PER, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // two point sets: sources pts2[0, n_src), queries pts2[n_src, n) with per-leaf ranges
+  const bool sets = L.n_src < L.n;
+  const float4* src = sets ? at<float4>(ws, L.pts2) : at<float4>(ws, L.pts);
+  const float4* qry = sets ? src + L.n_src : src;
+  const uint2* qrange = sets ? at<uint2>(ws, L.qrange) : nullptr;
   k_l2l_knn<KMAX, PER, LB><<<sms * 8, 32 * kL2LWarps, smem, s>>>(
-      at<float4>(ws, L.pts), at<NodeRec>(ws, L.nodes[0]), at<uint2>(ws, L.ilo[0]),
-      at<IEntry>(ws, L.arena), k, k_row, col0, kCtrWalk + pass, pl, order, idx, d2, m); note_launch();
+      src, at<NodeRec>(ws, L.nodes[0]), at<uint2>(ws, L.ilo[0]), at<IEntry>(ws, L.arena), k, k_row, col0,
+      kCtrWalk + pass, qry, qrange, pl, order, idx, d2, m); note_launch();
 }
 
 template <bool PER>

@@ -20,8 +20,10 @@ KNN_REL = 1e-6
 D2_ULPS = 2
 
 
-def check_knn(xyz, queries, gpu_idx, gpu_d2, ref_idx, ref_d2, periodic_L=0.0, rel=KNN_REL):
-    """Raise AssertionError with a short report if the rows disagree beyond the rule."""
+def check_knn(xyz, queries, gpu_idx, gpu_d2, ref_idx, ref_d2, periodic_L=0.0, rel=KNN_REL, query_xyz=None):
+    """Raise AssertionError with a short report if the rows disagree beyond the rule.
+    xyz holds the points the rows index; the query of row r is xyz[queries[r]], or
+    query_xyz[r] when the queries are a separate point set."""
     gpu_idx = np.asarray(gpu_idx).astype(np.int64)
     gpu_d2 = np.asarray(gpu_d2, dtype=np.float32)
     ref_idx = np.asarray(ref_idx).astype(np.int64)
@@ -31,7 +33,8 @@ def check_knn(xyz, queries, gpu_idx, gpu_d2, ref_idx, ref_d2, periodic_L=0.0, re
     n = np.asarray(xyz).shape[0]
     assert gpu_idx.min() >= 0 and gpu_idx.max() < n, "index out of range"
     x = np.asarray(xyz, dtype=np.float64)
-    d = x[gpu_idx] - x[q][:, None, :]
+    xq = x[q] if query_xyz is None else np.asarray(query_xyz, dtype=np.float64)
+    d = x[gpu_idx] - xq[:, None, :]
     if periodic_L > 0:
         d = d - periodic_L * np.round(d / periodic_L)
     g64 = np.sum(d * d, axis=-1)
