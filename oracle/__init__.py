@@ -367,3 +367,53 @@ def canonical_labels(labels) -> np.ndarray:
             first[v] = i
         out[i] = first[v]
     return out
+
+
+# ------------------------------------------------------------------ FoF catalogue
+
+def fof_catalogue(xyz, labels, periodic_L=0.0, vel=None, min_count=20, particle_mass=1.0):
+    """Catalogue reduction after FoF (Sec. IV-B), written from its definition.
+
+    Group order: a stable sort of the points in z order by the z position of their
+    group's root (the member with the lowest z position), so roots keep their z
+    order and every group is a contiguous block in z order.  Per group of at least
+    ``min_count`` points (in group order): mass = count * particle_mass; centre of
+    mass of the positions taken relative to the root by the minimum image (periodic)
+    and wrapped back into [0, L); inertia radius = sqrt of the mean squared distance
+    to the centre of mass; centre-of-mass velocity (zero without velocities).
+    Returns (order: original indices in group order, groups: list of dicts with
+    label, count, offset, mass, x_cm, v_cm, r_inertia), all float64.
+    """
+    x = np.asarray(xyz, dtype=np.float32)
+    lab = np.asarray(labels, dtype=np.int64)
+    n = x.shape[0]
+    _, zperm = zsort(morton_keys(x, periodic_L))  # z position -> original index
+    zpos = np.empty(n, dtype=np.int64)
+    zpos[zperm] = np.arange(n)
+    root = np.full(n, n, dtype=np.int64)  # per label: lowest z position of its members
+    np.minimum.at(root, lab, zpos)
+    zroot = root[lab[zperm]]  # root z position of the point at each z position
+    order = zperm[np.argsort(zroot, kind="stable")]
+    x64 = x.astype(np.float64)
+    v64 = None if vel is None else np.asarray(vel, dtype=np.float32).astype(np.float64)
+    groups = []
+    starts = np.flatnonzero(np.r_[True, lab[order[1:]] != lab[order[:-1]]])
+    ends = np.r_[starts[1:], n]
+    for s, e in zip(starts, ends):
+        cnt = int(e - s)
+        if cnt < min_count:
+            continue
+        mem = order[s:e]
+        ref = x64[mem[0]]
+        d = x64[mem] - ref
+        if periodic_L > 0:
+            d -= periodic_L * np.round(d / periodic_L)
+        dm = d.mean(axis=0)
+        xcm = ref + dm
+        if periodic_L > 0:
+            xcm = np.mod(xcm, periodic_L)
+        r2 = ((d - dm) ** 2).sum(axis=1).mean()
+        groups.append(dict(label=int(lab[mem[0]]), count=cnt, offset=int(s), mass=cnt * float(particle_mass),
+                           x_cm=xcm, v_cm=np.zeros(3) if v64 is None else v64[mem].mean(axis=0),
+                           r_inertia=float(np.sqrt(r2))))
+    return order, groups

@@ -403,3 +403,58 @@ def test_knn_sets_pins():
     assert np.array_equal(si, qi) and np.array_equal(sd, qd)
     qi, qd = oracle.knn_brute_sets(src, src[[5, 17]], 1, 0.0)
     assert list(qi[:, 0]) == [5, 17] and np.all(qd == 0.0)
+
+
+def test_fof_catalogue_pins():
+    """Catalogue: group order keeps roots in z order and members contiguous in z
+    order; counts and offsets partition the points; a two-point group across the
+    periodic boundary has its centre of mass on the boundary side and inertia radius
+    = half the separation; velocities average; groups below min_count drop."""
+    L = 1.0
+    x = np.array([[0.999, 0.5, 0.5], [0.001, 0.5, 0.5],   # pair across x = 0
+                  [0.25, 0.25, 0.25], [0.25, 0.25, 0.2578125], [0.25, 0.2578125, 0.25],  # triple
+                  [0.7, 0.1, 0.9]], dtype=np.float32)
+    x = workloads.snap_unit(x)
+    lab = oracle.fof_brute(x, 0.01, L)
+    v = np.arange(18, dtype=np.float32).reshape(6, 3)
+    order, groups = oracle.fof_catalogue(x, lab, L, vel=v, min_count=2)
+    assert sorted(order.tolist()) == list(range(6))
+    by = {g["label"]: g for g in groups}
+    assert set(by) == {0, 2} and by[0]["count"] == 2 and by[2]["count"] == 3
+    pair = by[0]
+    sep = (1.0 - float(x[0, 0])) + float(x[1, 0])
+    assert abs(pair["r_inertia"] - sep / 2) < 1e-12
+    assert min(pair["x_cm"][0], 1.0 - pair["x_cm"][0]) < 1e-3
+    assert np.allclose(pair["v_cm"], (v[0] + v[1]) / 2)
+    # contiguity and offsets: members of each group sit at [offset, offset + count)
+    for g in groups:
+        assert set(lab[order[g["offset"]:g["offset"] + g["count"]]]) == {g["label"]}
+    # group order: roots in z order, members in z order
+    _, zp = oracle.zsort(oracle.morton_keys(x, L))
+    zpos = np.empty(6, int)
+    zpos[zp] = np.arange(6)
+    zo = zpos[order]
+    rootz = np.array([min(zpos[lab == lab[i]]) for i in order])
+    assert np.all(np.diff(rootz) >= 0)
+    same = rootz[1:] == rootz[:-1]
+    assert np.all(np.diff(zo)[same] > 0)
+    # min_count drops small groups; singletons everywhere gives the z order itself
+    _, g20 = oracle.fof_catalogue(x, lab, L, min_count=20)
+    assert g20 == []
+    o1, _ = oracle.fof_catalogue(x, np.arange(6), L, min_count=1)
+    assert np.array_equal(o1, zp)
+
+
+def test_fof_catalogue_matches_direct_sums_on_clusters():
+    """Random clustered set: every catalogue entry equals a direct computation from
+    the members of its label (open box: plain mean and spread)."""
+    x = workloads.clustered(3000, 19, n_blobs=5)
+    lab = oracle.fof_brute(x, 0.004, 0.0)
+    order, groups = oracle.fof_catalogue(x, lab, 0.0, min_count=5, particle_mass=2.5)
+    assert groups
+    for g in groups:
+        mem = np.flatnonzero(lab == g["label"])
+        assert g["count"] == len(mem) and g["mass"] == 2.5 * len(mem)
+        p = x[mem].astype(np.float64)
+        assert np.allclose(g["x_cm"], p.mean(0), rtol=0, atol=1e-12)
+        assert abs(g["r_inertia"] - np.sqrt(((p - p.mean(0)) ** 2).sum(1).mean())) < 1e-12
