@@ -15,6 +15,7 @@ path here) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -430,6 +431,38 @@ def main():
     ms_step = max_over_ranks([ms_total / a.steps], dist, dev)[0]
     value = whole_job_rate(n, world, ms_step)
 
+    # FoF catalogue (Sec. IV-B): build + FoF + group order + reductions, groups >= 20
+    cat = None
+    try:
+        cap = n // 20 + 1
+        order_c = torch.empty(n, dtype=torch.int32, device=dev)
+        gbuf = torch.empty(cap * jzt.GROUP_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        ng = torch.zeros(1, dtype=torch.int64, device=dev)
+
+        def cat_step():
+            t2 = jzt.build(x_dev, periodic_L=L, workspace=ws, params=params)
+            jzt.lib.jzt_tree_fof_catalogue(t2._h, float(b), None, 20, 1.0, ctypes.c_void_p(lab.data_ptr()),
+                                           ctypes.c_void_p(order_c.data_ptr()), ctypes.c_void_p(gbuf.data_ptr()),
+                                           cap, ctypes.c_void_p(ng.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+            return t2
+        t2 = cat_step()
+        t2.status(raise_on_error=True)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(3):
+            t2 = cat_step()
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        t2.status(raise_on_error=True)
+        ms_cat = c0.elapsed_time(c1) / 3
+        cat = {"ms_per_step": ms_cat, "value": n / (ms_cat / 1000.0), "unit": UNIT, "min_count": 20,
+               "groups": int(ng.item()), "step": "build + FoF + group order + catalogue reduction"}
+        del order_c, gbuf, ng, t2
+    except Exception as exc:  # noqa: BLE001  (reported, not fatal for the main line)
+        cat = {"error": str(exc)[:200]}
+    jzt.profile_read()
+
     del ws, idx, d2, lab, tree
     torch.cuda.empty_cache()
 
@@ -541,7 +574,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
-            "clocks": clk, "e2e": e2e, "e2e_serial": e2e_serial, "gpu_launches": launches, "roofline": roofline,
+            "clocks": clk, "e2e": e2e, "e2e_serial": e2e_serial, "gpu_launches": launches,
+            "fof_catalogue": cat, "roofline": roofline,
             "roofline_sort": roof_sort, "roofline_build": roof_build,
             "phases_ms_per_step": {ph: phase_ms[ph] / steps for ph in phase_ms},
             "knn_particles_per_s": n / ((build_ms + knn_ms) / 1000.0) if knn_ms else None,

@@ -143,6 +143,36 @@ int jzt_knn_query(const float *d_src, int64_t n_src, const float *d_qry, int64_t
                   float periodic_L, int32_t *d_idx, float *d_dist2, void *d_ws, size_t ws_bytes,
                   void *stream);
 
+/* ---- FoF catalogue (Sec. IV-B, catalogue reduction). */
+typedef struct jzt_group {
+    int32_t label;        /* the group's FoF label (smallest original index) */
+    int32_t count;        /* points in the group */
+    int64_t offset;       /* position of the group's first point in d_order */
+    float mass;           /* count * particle_mass */
+    float x_cm[3];        /* centre of mass; periodic: of the minimum-image positions
+                             relative to the group's root, wrapped into [0, L) */
+    float v_cm[3];        /* centre-of-mass velocity (0 when d_vel is NULL) */
+    float r_inertia;      /* sqrt of the mean squared distance to x_cm */
+} jzt_group;             /* 48 bytes */
+
+/* FoF at linking length b (as jzt_tree_fof, labels into d_labels), then the
+ * catalogue: d_order (N int32) receives the original indices in group order -- a
+ * stable sort of the z-ordered points by the z position of their group's root
+ * (the member with the lowest z position), so roots keep their z order and every
+ * group is a contiguous block in z order -- and d_groups the groups of at least
+ * min_count points, in group order, up to cap_groups of them; *d_n_groups
+ * (device int64) receives their number.  More than cap_groups groups: the first
+ * cap_groups are written and the status reports JZT_ERR_CAPACITY.  Sums are
+ * taken in float64 in a fixed order (deterministic).  d_vel: N x 3 float32
+ * velocities in input order, or NULL.  Scratch comes from the interaction-list
+ * part of the workspace (about 36 bytes per point; JZT_ERR_WORKSPACE if it is
+ * smaller).  Errors as jzt_tree_fof, plus JZT_ERR_INVALID (min_count < 1,
+ * particle_mass not finite, null outputs, cap_groups < 0) and
+ * JZT_ERR_UNSUPPORTED on a query tree. */
+int jzt_tree_fof_catalogue(jzt_tree *t, float b, const float *d_vel, int min_count, float particle_mass,
+                           int32_t *d_labels, int32_t *d_order, jzt_group *d_groups, int64_t cap_groups,
+                           int64_t *d_n_groups, void *stream);
+
 /* One-call forms: build, then walk, on the same workspace. */
 int jzt_knn(const float *d_xyz, int64_t n, int k, float periodic_L,
             int32_t *d_idx, float *d_dist2, void *d_ws, size_t ws_bytes, void *stream);

@@ -42,7 +42,7 @@ SYMBOLS = ("jzt_workspace_bytes", "jzt_build", "jzt_tree_knn", "jzt_tree_fof", "
            "jzt_status", "jzt_tree_arrays", "jzt_tree_plane", "jzt_tree_free", "jzt_last_error",
            "jzt_version", "jzt_profile_enable", "jzt_profile_read", "jzt_profile_phase_name",
            "jzt_knn_noalloc", "jzt_batch_run", "jzt_workspace_bytes_query", "jzt_build_query",
-           "jzt_knn_query")
+           "jzt_knn_query", "jzt_tree_fof_catalogue")
 JZT_OP_KNN = 0
 JZT_OP_FOF = 1
 
@@ -108,7 +108,8 @@ def _load():
     lib.jzt_workspace_bytes_query.argtypes = [i64, i64, ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(sz)]
     lib.jzt_build_query.argtypes = [vp, i64, vp, i64, f32, ctypes.POINTER(Params), vp, sz, vp, ctypes.POINTER(vp)]
     lib.jzt_knn_query.argtypes = [vp, i64, vp, i64, ctypes.c_int, f32, vp, vp, vp, sz, vp]
-    for name in ("jzt_workspace_bytes_query", "jzt_build_query", "jzt_knn_query"):
+    lib.jzt_tree_fof_catalogue.argtypes = [vp, f32, vp, ctypes.c_int, f32, vp, vp, vp, i64, vp, vp]
+    for name in ("jzt_workspace_bytes_query", "jzt_build_query", "jzt_knn_query", "jzt_tree_fof_catalogue"):
         getattr(lib, name).restype = ctypes.c_int
     lib.jzt_tree_free.argtypes = [vp]
     lib.jzt_tree_free.restype = None
@@ -207,6 +208,15 @@ def profile_read() -> tuple[dict, dict, int]:
     return ({names[i]: ms[i] for i in range(n)}, {names[i]: cnt[i] for i in range(n)}, int(launches.value))
 
 
+def _group_dtype():
+    import numpy as np
+    return np.dtype([("label", "<i4"), ("count", "<i4"), ("offset", "<i8"), ("mass", "<f4"),
+                     ("x_cm", "<f4", (3,)), ("v_cm", "<f4", (3,)), ("r_inertia", "<f4")])
+
+
+GROUP_DTYPE = _group_dtype()  # jzt_group, 48 bytes
+
+
 class Tree:
     """A tree built in a caller-owned workspace (see jzt_build)."""
 
@@ -241,6 +251,30 @@ class Tree:
         _check(lib.jzt_tree_fof(self._h, float(b), ctypes.c_void_p(lab.data_ptr()),
                                 ctypes.c_void_p(_stream(stream))))
         return lab
+
+    def fof_catalogue(self, b: float, vel=None, min_count: int = 20, particle_mass: float = 1.0,
+                      cap_groups: int | None = None, stream=None):
+        """FoF labels plus the catalogue of groups with >= min_count points (jzt_tree_fof_catalogue).
+        Returns (labels [N] int32, order [N] int32 original indices in group order,
+        groups: host numpy structured array with GROUP_DTYPE fields, in group order)."""
+        import numpy as np
+        dev = self.workspace.device
+        n = self.n
+        cap = int(cap_groups) if cap_groups is not None else n // max(1, int(min_count)) + 1
+        labels = torch.empty(n, dtype=torch.int32, device=dev)
+        order = torch.empty(n, dtype=torch.int32, device=dev)
+        gbuf = torch.empty(max(cap, 1) * GROUP_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        ng = torch.zeros(1, dtype=torch.int64, device=dev)
+        if vel is not None:
+            _check_xyz(vel)
+        _check(lib.jzt_tree_fof_catalogue(self._h, float(b), ctypes.c_void_p(vel.data_ptr() if vel is not None else 0),
+                                          int(min_count), float(particle_mass), ctypes.c_void_p(labels.data_ptr()),
+                                          ctypes.c_void_p(order.data_ptr()), ctypes.c_void_p(gbuf.data_ptr()), cap,
+                                          ctypes.c_void_p(ng.data_ptr()), ctypes.c_void_p(_stream(stream))))
+        self.status(stream, raise_on_error=True)
+        k = min(int(ng.item()), cap)
+        groups = np.frombuffer(gbuf[:k * GROUP_DTYPE.itemsize].cpu().numpy().tobytes(), dtype=GROUP_DTYPE)
+        return labels, order, groups
 
     def arrays(self):
         """(sorted keys uint64 view as int64 [N], sorted points float32 [N,4], n_planes)."""

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libjzt.so")
 OBJDIR = os.path.join(ROOT, "_build", "obj")
-SOURCES = ["api.cu", "build_tree.cu", "walk_knn.cu", "walk_fof.cu", "prof.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["api.cu", "build_tree.cu", "walk_knn.cu", "walk_fof.cu", "prof.cu", "noalloc.cu", "batch.cu",
+           "catalogue.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills",
          f"-I{os.path.join(ROOT, 'include')}"]

@@ -323,6 +323,31 @@ int jzt_knn(const float* d_xyz, int64_t n, int k, float periodic_L, int32_t* d_i
   return e;
 }
 
+int jzt_tree_fof_catalogue(jzt_tree* t, float b, const float* d_vel, int min_count, float particle_mass,
+                           int32_t* d_labels, int32_t* d_order, jzt_group* d_groups, int64_t cap_groups,
+                           int64_t* d_n_groups, void* stream) {
+  if (!t) return fail(JZT_ERR_INVALID, "tree is null");
+  if (t->n_src < t->n) return fail(JZT_ERR_UNSUPPORTED, "FoF runs on a tree of one point set");
+  if (!d_labels || !d_order || !d_n_groups || (cap_groups > 0 && !d_groups))
+    return fail(JZT_ERR_INVALID, "null output pointer");
+  if (cap_groups < 0) return fail(JZT_ERR_INVALID, "cap_groups must be >= 0");
+  if (min_count < 1) return fail(JZT_ERR_INVALID, "min_count must be >= 1");
+  if (!std::isfinite(particle_mass)) return fail(JZT_ERR_INVALID, "particle_mass must be finite");
+  if (!(b > 0.0f) || std::isinf(b)) return fail(JZT_ERR_INVALID, "b must be positive and finite");
+  if (t->periodic_L > 0.0f && !(b < 0.5f * t->periodic_L))
+    return fail(JZT_ERR_INVALID, "periodic boxes need b < L/2");
+  if (catalogue_scratch_bytes(t->n) > sizeof(IEntry) * (size_t)t->L.cap_ilist)
+    return fail(JZT_ERR_WORKSPACE, "workspace too small for the catalogue scratch");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  launch_fof(t->L, t->ws, t->periodic_L, b, d_labels, s);
+  if (int e = launch_catalogue(t->L, t->ws, t->periodic_L, d_vel, min_count, particle_mass, d_order, d_groups,
+                               cap_groups, d_n_groups, s))
+    return e;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "jzt_tree_fof_catalogue launch");
+  return JZT_OK;
+}
+
 int jzt_knn_query(const float* d_src, int64_t n_src, const float* d_qry, int64_t n_qry, int k, float periodic_L,
                   int32_t* d_idx, float* d_dist2, void* d_ws, size_t ws_bytes, void* stream) {
   if (k < 1 || k > kMaxKTotal || (int64_t)k > n_src) {

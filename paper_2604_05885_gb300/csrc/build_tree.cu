@@ -1036,6 +1036,62 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
 
 }  // namespace
 
+namespace {
+
+__global__ void k_sort_prep(Meta* m) {
+  for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) (&m->radix_hist[0][0])[i] = 0;
+  if (threadIdx.x < kRadixPasses) m->tile_ctr[threadIdx.x] = 0;
+}
+
+// Digit histograms of the first `passes` 8-bit digits of keys.
+__global__ void __launch_bounds__(256) k_key_hist(const uint64_t* __restrict__ keys, int64_t n, int passes, Meta* m) {
+  __shared__ uint32_t sh[kRadixPasses][kRadixBins];
+  for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k >> (p * kRadixBits)) & (kRadixBins - 1)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadixBins; i += blockDim.x) {
+    const uint32_t v = (&sh[0][0])[i];
+    if (v) atomicAdd(&m->radix_hist[0][0] + i, v);
+  }
+}
+
+}  // namespace
+
+// Stable LSD sort of (k_a, index) by the low 8 * passes bits of k_a (passes even,
+// at most 8): the sorted keys end in k_a and the indices in v_a; k_b and v_b are
+// the ping-pong buffers; lookback holds passes * n_tiles * 256 words.  Uses the
+// radix counters of the status block m (not during a build).
+void launch_sort_u64(uint64_t* k_a, uint64_t* k_b, uint32_t* v_a, uint32_t* v_b, int64_t n, int passes,
+                     uint32_t* lookback, cudaStream_t s, Meta* m) {
+  const int sms = 152;
+  const int64_t n_tiles = (n + kSortTile - 1) / kSortTile;
+  k_sort_prep<<<1, 256, 0, s>>>(m); note_launch();
+  k_key_hist<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(k_a, n, passes, m); note_launch();
+  k_radix_offsets<<<1, 32 * kRadixPasses, 0, s>>>(m); note_launch();
+  const int64_t lb_words = n_tiles * kRadixBins * passes;
+  k_zero_u64<<<grid_for(lb_words / 2 + 1, 256, sms * 8), 256, 0, s>>>(
+      reinterpret_cast<unsigned long long*>(lookback), (lb_words + 1) / 2); note_launch();
+  const size_t smem = sizeof(SortSmem);
+  cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const uint64_t* kin = k_a;
+  const uint32_t* vin = nullptr;
+  uint64_t* kout = k_b;
+  uint32_t* vout = v_b;
+  for (int p = 0; p < passes; ++p) {
+    k_onesweep<<<(unsigned)n_tiles, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, p,
+                                                             lookback + (size_t)p * n_tiles * kRadixBins, m);
+    note_launch();
+    kin = kout;
+    vin = vout;
+    kout = (kout == k_b) ? k_a : k_b;
+    vout = (vout == v_b) ? v_a : v_b;
+  }
+}
+
 void launch_build(const float* d_xyz, int64_t n, float periodic_L, const Layout& L, char* ws, cudaStream_t s) {
   build_impl(d_xyz, n, nullptr, 0, periodic_L, L, ws, s);
 }

@@ -155,6 +155,12 @@ void launch_fof(const Layout& L, char* ws, float periodic_L, float b, int32_t* d
                 cudaStream_t s);
 // shared (build_tree.cu)
 void launch_super_level(const Layout& L, char* ws, cudaStream_t s);
+size_t catalogue_scratch_bytes(int64_t n);
+int launch_catalogue(const Layout& L, char* ws, float periodic_L, const float* d_vel, int min_count,
+                     float particle_mass, int32_t* d_order, jzt_group* d_groups, int64_t cap_groups,
+                     int64_t* d_n_groups, cudaStream_t s);
+void launch_sort_u64(uint64_t* k_a, uint64_t* k_b, uint32_t* v_a, uint32_t* v_b, int64_t n, int passes,
+                     uint32_t* lookback, cudaStream_t s, Meta* m);
 
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
