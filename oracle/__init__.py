@@ -316,16 +316,61 @@ def num_planes(n: int, nmax0: int = 48, c: int = 8, n_target: int = 1000) -> int
     return p
 
 
-def plane_splits(skeys, nmax0: int = 48, c: int = 8, n_target: int = 1000, n_planes=None):
+VOLUME_BINS = 97  # node-volume classes: 0 = single point, 1 + (level + 32) = volume 2^level
+
+
+def node_level_bins(lvl, gaps):
+    """Volume class of every node [gaps[j], gaps[j+1]) of a plane: 0 for a single
+    point (no extent), else 1 + 32 + the largest gap level inside the node."""
+    out = np.zeros(len(gaps) - 1, dtype=np.int64)
+    for j in range(len(gaps) - 1):
+        a, b = int(gaps[j]), int(gaps[j + 1])
+        if b - a >= 2:
+            out[j] = 1 + 32 + int(np.max(lvl[a + 1:b]))
+    return out
+
+
+def regularization_level(counts, bins, n, f_max):
+    """lvl_max of Sec. II-D: 2^lvl_max <= f_max V_90%, V_90% = point-weighted mean
+    node volume over the smallest nodes that together hold 90 % of the points.
+    Reading: nodes are taken by volume class, smallest first; within the class
+    that reaches 90 % only the points still needed are counted.  Evaluated in
+    float64 in exactly this order (volume 2^level, single points volume 0);
+    returns None (no regularisation) when V_90% is 0."""
+    hist = np.zeros(VOLUME_BINS, dtype=np.int64)
+    np.add.at(hist, bins, counts)
+    target = 0.9 * float(n)
+    acc = 0.0
+    cum = 0
+    for b in range(VOLUME_BINS):
+        if hist[b] == 0:
+            continue
+        vol = 0.0 if b == 0 else float(np.ldexp(1.0, b - 33))
+        if float(cum + hist[b]) >= target:
+            acc = acc + (target - float(cum)) * vol
+            break
+        acc = acc + float(hist[b]) * vol
+        cum += int(hist[b])
+    v90 = acc / target
+    x = float(np.float32(f_max)) * v90
+    if not x > 0.0:
+        return None
+    return int(np.frexp(x)[1]) - 1  # floor(log2(x))
+
+
+def plane_splits(skeys, nmax0: int = 48, c: int = 8, n_target: int = 1000, n_planes=None, f_max: float = 0.0):
     """Tree-plane splits (Sec. II-C, Fig. tree_construction).
 
     Returns (spl, gaps): spl[p] holds the splits of plane p -- point indices for
     p = 0 and indices into plane p-1's node array for p >= 1 -- and gaps[p] the
     point-space gap index of every split.  A gap is a split of plane p when its
-    n exceeds N_max^(p) = N_max^(0) c^p; the first and last gap always are."""
+    n exceeds N_max^(p) = N_max^(0) c^p; the first and last gap always are.
+    f_max > 0 adds the regularisation of Sec. II-D: after the count splits of a
+    plane, every candidate gap whose level exceeds lvl_max^(p) is kept as well."""
     k = np.asarray(skeys, dtype=np.uint64)
     n = k.shape[0]
     nsz = node_sizes(k)
+    lvl = gap_levels(k)
     if n_planes is None:
         n_planes = num_planes(n, nmax0, c, n_target)
     gaps = []
@@ -336,6 +381,11 @@ def plane_splits(skeys, nmax0: int = 48, c: int = 8, n_target: int = 1000, n_pla
         keep = nsz[cand] > nmax
         keep[0] = True
         keep[-1] = True
+        if f_max > 0 and n > 1:
+            g0 = cand[np.nonzero(keep)[0]]
+            lmax = regularization_level(np.diff(g0), node_level_bins(lvl, g0), n, f_max)
+            if lmax is not None:
+                keep |= lvl[cand] > lmax
         pos = np.nonzero(keep)[0]
         spl.append(pos.astype(np.int64))
         cand = cand[pos]

@@ -458,3 +458,35 @@ def test_fof_catalogue_matches_direct_sums_on_clusters():
         p = x[mem].astype(np.float64)
         assert np.allclose(g["x_cm"], p.mean(0), rtol=0, atol=1e-12)
         assert abs(g["r_inertia"] - np.sqrt(((p - p.mean(0)) ** 2).sum(1).mean())) < 1e-12
+
+
+def test_regularisation_pins():
+    """Sec. II-D in the oracle: f_max = 0 or huge leaves the planes unchanged; with
+    regularisation no node of a plane has level above lvl_max^(p) unless it is one
+    point; the lvl_max value equals an independent computation (points expanded by
+    node volume, sorted, the first 90 % averaged)."""
+    rng = np.random.default_rng(12)
+    x = workloads.clip_unit(np.concatenate([rng.normal(0.5, 0.01, (3000, 3)), rng.random((30, 3))]))
+    sk, _ = oracle.zsort(oracle.morton_keys(x, 0.0))
+    plain = oracle.plane_splits(sk, 32, 8, 20)[1]
+    for f in (0.0, 1e30):
+        got = oracle.plane_splits(sk, 32, 8, 20, f_max=f)[1]
+        assert all(np.array_equal(a, b) for a, b in zip(got, plain))
+    lvl = oracle.gap_levels(sk)
+    reg = oracle.plane_splits(sk, 32, 8, 20, f_max=50.0)[1]
+    assert len(reg[0]) > len(plain[0])
+    # lvl_max of plane 0 from its count splits, independently
+    g0 = plain[0]
+    cnt = np.diff(g0)
+    bins = oracle.node_level_bins(lvl, g0)
+    vols = np.where(bins == 0, 0.0, np.ldexp(1.0, bins - 33))
+    per_point = np.sort(np.repeat(vols, cnt))
+    m = 0.9 * len(sk)
+    whole = int(np.floor(m))
+    v90 = (per_point[:whole].sum() + (m - whole) * per_point[whole]) / m
+    lmax = int(np.floor(np.log2(50.0 * v90)))
+    assert oracle.regularization_level(cnt, bins, len(sk), 50.0) == lmax
+    # every regularised leaf with two or more points lies inside a cell of level <= lmax
+    for a, b in zip(reg[0][:-1], reg[0][1:]):
+        if b - a >= 2:
+            assert lvl[a + 1:b].max() <= lmax
