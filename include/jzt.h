@@ -60,7 +60,10 @@ typedef struct jzt_params {
     float alloc_fac_nodes;    /* node capacity per plane = fac * N / (N_max^(p)/2) (default 2; Eq. alloc_nodes) */
     float alloc_fac_ilist;    /* interaction-list capacity = fac * N / (N_max^(0)/2) (default 128; Eq. alloc_ilist) */
     int32_t heap_size;        /* N_r: entries of the FindRmax register heap, 2..16 (default 8; Alg. 3) */
-    int32_t reserved[7];      /* must be zero */
+    float reg_fmax;           /* f_max of the plane regularisation (Sec. II-D): 0 = off (default);
+                                 > 0: every plane also splits wherever a gap's level exceeds
+                                 lvl_max^(p), 2^lvl_max <= f_max V_90% -- results do not change */
+    int32_t reserved[6];      /* must be zero */
 } jzt_params;
 
 typedef struct jzt_tree jzt_tree;  /* opaque; lives on the host, points into the workspace */

@@ -58,7 +58,7 @@ class Params(ctypes.Structure):
     _fields_ = [("nmax0", ctypes.c_int32), ("plane_factor", ctypes.c_int32),
                 ("n_target", ctypes.c_int32), ("ngr", ctypes.c_int32),
                 ("alloc_fac_nodes", ctypes.c_float), ("alloc_fac_ilist", ctypes.c_float),
-                ("heap_size", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("heap_size", ctypes.c_int32), ("reg_fmax", ctypes.c_float), ("reserved", ctypes.c_int32 * 6)]
 
 
 class Job(ctypes.Structure):

@@ -34,8 +34,9 @@ int resolve_params(const jzt_params* p, Params* out, const char** why) {
   P.heap = 8;
   P.fac_nodes = 2.0f;
   P.fac_ilist = 128.0f;
+  P.reg_fmax = 0.0f;
   if (p) {
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 6; ++i)
       if (p->reserved[i] != 0) {
         *why = "jzt_params.reserved must be zero";
         return JZT_ERR_INVALID;
@@ -47,6 +48,11 @@ int resolve_params(const jzt_params* p, Params* out, const char** why) {
     if (p->heap_size) P.heap = p->heap_size;
     if (p->alloc_fac_nodes != 0.0f) P.fac_nodes = p->alloc_fac_nodes;
     if (p->alloc_fac_ilist != 0.0f) P.fac_ilist = p->alloc_fac_ilist;
+    P.reg_fmax = p->reg_fmax;
+  }
+  if (!(P.reg_fmax >= 0.0f) || std::isinf(P.reg_fmax)) {
+    *why = "reg_fmax must be >= 0 and finite";
+    return JZT_ERR_INVALID;
   }
   if (P.nmax0 < 1 || P.nmax0 > 32) { *why = "nmax0 must be in 1..32"; return JZT_ERR_INVALID; }
   if (P.c < 2 || P.c > 64) { *why = "plane_factor must be in 2..64"; return JZT_ERR_INVALID; }
@@ -85,6 +91,7 @@ int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* L
   L.n_target = P.n_target;
   L.ngr = P.ngr;
   L.heap = P.heap;
+  L.reg_fmax = P.reg_fmax;
   L.n_planes = num_planes(n, P);
   // Node capacity per plane: fac * N / (N_max^(p)/2) (Eq. alloc_nodes).  The
   // estimate is not a bound (Sec. II-C), so the small upper planes get 4x the

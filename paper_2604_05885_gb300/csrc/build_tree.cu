@@ -126,7 +126,11 @@ __global__ void k_init_meta(Meta* m, int n_planes) {
     m->pair_off[t] = 0;
     m->pair_cnt[t] = 0;
   }
-  if (t < kMaxPlanes) m->knn_plane_entries[t] = 0;
+  if (t < kMaxPlanes) {
+    m->knn_plane_entries[t] = 0;
+    m->reg_lvl[t] = kNoRegLevel;
+  }
+  if (t < kVolBins) m->vol_hist[t] = 0;
   if (t < 8) m->knn_stats[t] = 0;
   if (t == 0) {
     m->knn_pairs = 0;
@@ -633,6 +637,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const uint64_t* _
   __shared__ uint64_t s_key[kScanTile + 2 * 32 + 1];
   __shared__ int8_t s_w[kScanTile + 32];
   __shared__ uint32_t s_tile;
+  const int reg_lvl = m->reg_lvl[0];
   if (threadIdx.x == 0) s_tile = atomicAdd(&m->tile_ctr[kCtrLeafSplits], 1u);
   __syncthreads();
   const int64_t tile = s_tile;
@@ -664,7 +669,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const uint64_t* _
     } else if (i < n) {
       int li = (int)(i - k0);  // s_key index of point i
       int g = level_ext(s_key[li - 1], s_key[li], i - 1, i);
-      int64_t jlo = max64(0, i - M), jhi = min64(i - 1, n - 1 - M);
+      f = g > reg_lvl;  // regularisation (Sec. II-D); reg_lvl = 127 when off
+      int64_t jlo = f ? 1 : max64(0, i - M), jhi = f ? 0 : min64(i - 1, n - 1 - M);
       for (int64_t j = jlo; j <= jhi; ++j) {
         if (s_w[j - k0] <= g) {
           f = true;
@@ -766,14 +772,72 @@ __global__ void k_split_sizes(const uint64_t* __restrict__ keys, int64_t n,
 // Plane p >= 1: keep the plane p-1 splits whose n exceeds N_max^(p) (plus the
 // two ends); spl[p] holds their positions in plane p-1's split array, gap[p]
 // and nsz[p] carry the point-space gap index and n along.
+// ---------------------------------------------------------------- regularisation
+// Points per node-volume class of plane p (nodes [gap[j], gap[j+1])): 0 for one
+// point, else 1 + 32 + level of the node (the level of its first and last point,
+// the largest gap level inside it).
+__global__ void k_vol_hist(const uint64_t* __restrict__ keys, const int32_t* __restrict__ gap, int plane,
+                           Meta* m) {
+  __shared__ unsigned long long sh[kVolBins];
+  for (int i = threadIdx.x; i < kVolBins; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const int64_t nn = m->n_nodes[plane];
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nn; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = gap[j], b = gap[j + 1];
+    const int bin = b - a >= 2 ? 1 + 32 + level_ext(keys[a], keys[b - 1], a, b - 1) : 0;
+    atomicAdd(&sh[bin], (unsigned long long)(b - a));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kVolBins; i += blockDim.x)
+    if (sh[i]) atomicAdd(&m->vol_hist[i], sh[i]);
+}
+
+// lvl_max^(p): 2^lvl_max <= f_max V_90%, V_90% = point-weighted mean node volume
+// over the smallest nodes holding 90 % of the points (whole volume classes from
+// the smallest; of the class that reaches 90 % only the points still needed).
+// float64 in this exact order, no fused operations.  Clears the histogram.
+__global__ void k_reg_level(int plane, int64_t n, float f_max, Meta* m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double target = __dmul_rn(0.9, (double)n);
+  double acc = 0.0;
+  long long cum = 0;
+  for (int b = 0; b < kVolBins; ++b) {
+    const long long h = (long long)m->vol_hist[b];
+    if (h == 0) continue;
+    const double vol = b == 0 ? 0.0 : ldexp(1.0, b - 33);
+    if ((double)(cum + h) >= target) {
+      acc = __dadd_rn(acc, __dmul_rn(__dsub_rn(target, (double)cum), vol));
+      break;
+    }
+    acc = __dadd_rn(acc, __dmul_rn((double)h, vol));
+    cum += h;
+  }
+  const double v90 = __ddiv_rn(acc, target);
+  const double x = __dmul_rn((double)f_max, v90);
+  int e = 0;
+  if (x > 0.0) {
+    (void)frexp(x, &e);
+    m->reg_lvl[plane] = e - 1;
+  } else {
+    m->reg_lvl[plane] = kNoRegLevel;
+  }
+  for (int b = 0; b < kVolBins; ++b) m->vol_hist[b] = 0;
+}
+
+__global__ void k_reset_ctr(Meta* m, int ctr) {
+  if (threadIdx.x == 0) m->tile_ctr[ctr] = 0;
+}
+
 __global__ void __launch_bounds__(256) k_coarse_splits(const int32_t* __restrict__ gap_in,
                                                        const int32_t* __restrict__ nsz_in,
                                                        int plane_in, int64_t nmax, int32_t* spl,
                                                        int32_t* gap_out, int32_t* nsz_out,
                                                        int64_t cap, unsigned long long* st,
-                                                       int ctr, Meta* m) {
+                                                       int ctr, const uint64_t* __restrict__ keys,
+                                                       int64_t n, Meta* m) {
   constexpr int PER = kScanTile / 256;
   __shared__ uint32_t s_tile;
+  const int reg_lvl = m->reg_lvl[plane_in + 1];
   if (threadIdx.x == 0) s_tile = atomicAdd(&m->tile_ctr[ctr], 1u);
   __syncthreads();
   const int64_t tile = s_tile;
@@ -785,7 +849,13 @@ __global__ void __launch_bounds__(256) k_coarse_splits(const int32_t* __restrict
   for (int r = 0; r < PER; ++r) {
     int64_t t = t0 + r;
     bool f = false;
-    if (t < nin) f = (t == 0) || (t == nin - 1) || ((int64_t)nsz_in[t] > nmax);
+    if (t < nin) {
+      f = (t == 0) || (t == nin - 1) || ((int64_t)nsz_in[t] > nmax);
+      if (!f && reg_lvl != kNoRegLevel) {  // regularisation (Sec. II-D)
+        const int64_t g = gap_in[t];
+        f = g > 0 && g < n && level_ext(keys[g - 1], keys[g], g - 1, g) > reg_lvl;
+      }
+    }
     flags |= (uint32_t)f << r;
     cnt += f;
   }
@@ -990,21 +1060,37 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
   // plane 0: leaf splits, then n_i at every leaf split
   unsigned long long* st = at<unsigned long long>(ws, L.scan_flags);
   const int64_t split_tiles = (n + 1 + kScanTile - 1) / kScanTile;
-  k_zero_u64<<<grid_for(split_tiles, 256, sms * 8), 256, 0, s>>>(st, split_tiles); note_launch();
-  k_leaf_splits<<<(unsigned)split_tiles, kSplitThreads, 0, s>>>(
-      keys_a, n, L.nmax0, at<int32_t>(ws, L.spl[0]), L.cap_nodes[0], st, m); note_launch();
-  k_split_sizes<<<grid_for(L.cap_nodes[0] + 1, 256, sms * 16), 256, 0, s>>>(
-      keys_a, n, at<int32_t>(ws, L.spl[0]), at<int32_t>(ws, L.nsz[0]), m); note_launch();
+  const bool reg = L.reg_fmax > 0.0f;
+  // regularisation (Sec. II-D): after a plane's count splits, the volume classes
+  // of its nodes give lvl_max^(p); the plane's splits are then taken again with
+  // the level criterion added
+  auto regularise = [&](int p) {
+    k_vol_hist<<<grid_for(L.cap_nodes[p], 256, sms * 8), 256, 0, s>>>(keys_a, at<int32_t>(ws, L.gap[p]), p, m);
+    k_reg_level<<<1, 32, 0, s>>>(p, n, L.reg_fmax, m);
+    k_reset_ctr<<<1, 32, 0, s>>>(m, p == 0 ? kCtrLeafSplits : kCtrCoarse + p);
+    note_launch(3);
+  };
+  for (int pass = 0; pass < (reg ? 2 : 1); ++pass) {
+    if (pass == 1) regularise(0);
+    k_zero_u64<<<grid_for(split_tiles, 256, sms * 8), 256, 0, s>>>(st, split_tiles); note_launch();
+    k_leaf_splits<<<(unsigned)split_tiles, kSplitThreads, 0, s>>>(
+        keys_a, n, L.nmax0, at<int32_t>(ws, L.spl[0]), L.cap_nodes[0], st, m); note_launch();
+    k_split_sizes<<<grid_for(L.cap_nodes[0] + 1, 256, sms * 16), 256, 0, s>>>(
+        keys_a, n, at<int32_t>(ws, L.spl[0]), at<int32_t>(ws, L.nsz[0]), m); note_launch();
+  }
   // coarser planes
   int64_t nmax = L.nmax0;
   for (int p = 1; p < L.n_planes; ++p) {
     nmax *= L.c;
     const int64_t tiles = (L.cap_nodes[p - 1] + 1 + kScanTile - 1) / kScanTile;
-    k_zero_u64<<<grid_for(tiles, 256, sms * 8), 256, 0, s>>>(st, tiles); note_launch();
-    k_coarse_splits<<<(unsigned)tiles, 256, 0, s>>>(
-        at<int32_t>(ws, L.gap[p - 1]), at<int32_t>(ws, L.nsz[p - 1]), p - 1, nmax,
-        at<int32_t>(ws, L.spl[p]), at<int32_t>(ws, L.gap[p]), at<int32_t>(ws, L.nsz[p]),
-        L.cap_nodes[p], st, kCtrCoarse + p, m); note_launch();
+    for (int pass = 0; pass < (reg ? 2 : 1); ++pass) {
+      if (pass == 1) regularise(p);
+      k_zero_u64<<<grid_for(tiles, 256, sms * 8), 256, 0, s>>>(st, tiles); note_launch();
+      k_coarse_splits<<<(unsigned)tiles, 256, 0, s>>>(
+          at<int32_t>(ws, L.gap[p - 1]), at<int32_t>(ws, L.nsz[p - 1]), p - 1, nmax,
+          at<int32_t>(ws, L.spl[p]), at<int32_t>(ws, L.gap[p]), at<int32_t>(ws, L.nsz[p]),
+          L.cap_nodes[p], st, kCtrCoarse + p, keys_a, n, m); note_launch();
+    }
   }
   prof_end(kPhSplits, s);
   prof_begin(kPhNodes, s);

@@ -43,6 +43,11 @@ enum Stage : int32_t {
 };
 
 // Device-resident status and bookkeeping; lives at offset 0 of the workspace.
+// Node-volume classes of the regularisation: 0 = one point (no extent), else
+// 1 + 32 + level (volume 2^level; levels -32..63 with the extended equal-key levels).
+constexpr int kVolBins = 97;
+constexpr int kNoRegLevel = 127;
+
 struct Meta {
   int32_t status;            // jzt_error of the first failure (0 = ok)
   int32_t detail;            // Stage of the first failure
@@ -65,12 +70,15 @@ struct Meta {
   unsigned long long pair_cnt[kMaxPlanes + 1];
   uint32_t radix_offsets[kRadixPasses][kRadixBins];  // exclusive digit offsets per pass
   uint32_t radix_hist[kRadixPasses][kRadixBins];     // digit histograms per pass
+  int32_t reg_lvl[kMaxPlanes];       // regularisation: lvl_max per plane (127 = none)
+  unsigned long long vol_hist[kVolBins];  // points per node-volume class of one plane
 };
 
 // Workspace layout: byte offsets of every sub-buffer (host-computed).
 struct Layout {
   int64_t n;
   int32_t nmax0, c, n_target, ngr, heap;
+  float reg_fmax;                     // 0: no regularisation
   int32_t n_planes;
   int64_t cap_nodes[kMaxPlanes + 1];  // [n_planes] = super-node capacity
   int64_t cap_ilist;                  // entries
@@ -115,6 +123,7 @@ struct __align__(8) IEntry {
 struct Params {
   int32_t nmax0, c, n_target, ngr, heap;
   float fac_nodes, fac_ilist;
+  float reg_fmax;
 };
 
 // ---------------------------------------------------------------- host API

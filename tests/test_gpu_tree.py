@@ -10,6 +10,11 @@ from tests.gpu_util import to_dev
 pytestmark = pytest.mark.gpu
 
 
+def _gauss_outliers(seed=7):
+    rng = np.random.default_rng(seed)
+    return workloads.clip_unit(np.concatenate([rng.normal(0.5, 0.01, (6000, 3)), rng.random((60, 3))]))
+
+
 def _cases():
     x_dup = workloads.uniform(3000, 4)
     x_dup[100:400] = x_dup[100]          # a run of 300 identical points
@@ -28,7 +33,12 @@ def _cases():
         ("tiny-2", workloads.uniform(2, 6), 1.0, None),
         ("tiny-33", workloads.uniform(33, 6), 0.0, None),
         ("ragged-tiles", workloads.uniform(4096 * 3 + 17, 8), 0.0, dict(nmax0=5, n_target=30)),
+        # regularisation (Sec. II-D): a dense Gaussian with far outliers, and the duplicates case
+        ("reg-gauss-outliers", _gauss_outliers(), 0.0, dict(n_target=20, reg_fmax=50.0)),
+        ("reg-gauss-periodic", _gauss_outliers(8), 1.0, dict(nmax0=16, n_target=8, reg_fmax=4.0)),
+        ("reg-duplicates", x_dup, 0.0, dict(nmax0=8, plane_factor=4, n_target=4, reg_fmax=1.0)),
     ]
+
 
 
 @pytest.mark.parametrize("name,x,L,params", _cases(), ids=[c[0] for c in _cases()])
@@ -49,7 +59,10 @@ def test_tree_matches_oracle(name, x, L, params):
     p_np = pts.cpu().numpy()
     assert np.array_equal(p_np[:, 3].view(np.int32), perm.astype(np.int32))
     assert np.array_equal(p_np[:, :3], x[perm])
-    spl_ref, gaps_ref = oracle.plane_splits(sk, nmax0=nmax0, c=c, n_target=nt)
+    spl_ref, gaps_ref = oracle.plane_splits(sk, nmax0=nmax0, c=c, n_target=nt, f_max=p.get("reg_fmax", 0.0))
+    if p.get("reg_fmax"):
+        plain = oracle.plane_splits(sk, nmax0=nmax0, c=c, n_target=nt)[1]
+        assert any(len(a) != len(b) for a, b in zip(gaps_ref, plain)), "regularisation added no split"
     nodes_ref = oracle.plane_nodes(x[perm], gaps_ref)
     for pl in range(n_planes):
         spl, cnt, box = tree.plane(pl)
@@ -69,3 +82,18 @@ def test_invalid_coordinates_set_input_status():
     x[3, 0] = 1.0  # outside [0, L) for L = 1
     tree = jzt.build(to_dev(x), periodic_L=1.0)
     assert tree.status()["code"] == jzt.JZT_ERR_INPUT
+
+
+def test_regularisation_leaves_results_unchanged():
+    """Sec. II-D: the regularisation changes the tree only, never the kNN rows or FoF labels."""
+    import paper_2604_05885_gb300 as jzt
+    x = _gauss_outliers(11)
+    for L in (0.0, 1.0):
+        a = jzt.build(to_dev(x), periodic_L=L)
+        r = jzt.build(to_dev(x), periodic_L=L, params=dict(reg_fmax=50.0))
+        ia, da = a.knn(16)
+        ir, dr = r.knn(16)
+        assert np.array_equal(ia.cpu().numpy(), ir.cpu().numpy())
+        assert np.array_equal(da.cpu().numpy(), dr.cpu().numpy())
+        b = 0.3 * workloads.mean_spacing(len(x))
+        assert np.array_equal(a.fof(b).cpu().numpy(), r.fof(b).cpu().numpy())
