@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--n-side", type=int, default=512)
     ap.add_argument("--k", type=int, default=16)
     ap.add_argument("--b-frac", type=float, default=0.2)
-    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--ref-side", type=float, default=0.25,
                     help="side of the sub-cube timed per step by --impl reference")
     ap.add_argument("--cpu-side", type=float, default=0.75,
@@ -402,9 +402,11 @@ def main():
         tree.fof(b, out=lab)
         return tree
 
+    tree = None
     for _ in range(a.warmup):
         tree = step(x_dev)
-    st = tree.status(raise_on_error=True)
+    if tree is not None:
+        tree.status(raise_on_error=True)
     jzt.profile_read()  # discard warm-up records
 
     def barrier():
