@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
                                                            int k_row, int col0, int ctr,
                                                            const float4* __restrict__ qpts,
                                                            const uint2* __restrict__ qrange,
-                                                           float L, int order,
+                                                           int vec_out, float L, int order,
                                                            int32_t* __restrict__ out_idx,
                                                            float* __restrict__ out_d2, Meta* m) {
   extern __shared__ __align__(16) unsigned char l2l_smem[];
@@ -1110,11 +1110,23 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
       const int64_t row = order == 0 ? (int64_t)__float_as_int(qp.w) : (int64_t)(qfirst + qi);
       int32_t* oi = out_idx + row * k_row + col0;
       float* od = out_d2 + row * k_row + col0;
+      if (vec_out && k == KMAX) {  // whole rows as 16-byte stores (aligned rows, k a multiple of 4)
 #pragma unroll
-      for (int e = 0; e < KMAX; ++e) {
-        if (e >= KMAX - k) {
-          oi[e - (KMAX - k)] = (int32_t)(uint32_t)(T.t[e] & 0xffffffffull) - 1;
-          od[e - (KMAX - k)] = __uint_as_float((uint32_t)(T.t[e] >> 32));
+        for (int e = 0; e < KMAX; e += 4) {
+          reinterpret_cast<int4*>(oi)[e / 4] =
+              make_int4((int32_t)(uint32_t)(T.t[e] & 0xffffffffull) - 1, (int32_t)(uint32_t)(T.t[e + 1] & 0xffffffffull) - 1,
+                        (int32_t)(uint32_t)(T.t[e + 2] & 0xffffffffull) - 1, (int32_t)(uint32_t)(T.t[e + 3] & 0xffffffffull) - 1);
+          reinterpret_cast<float4*>(od)[e / 4] =
+              make_float4(__uint_as_float((uint32_t)(T.t[e] >> 32)), __uint_as_float((uint32_t)(T.t[e + 1] >> 32)),
+                          __uint_as_float((uint32_t)(T.t[e + 2] >> 32)), __uint_as_float((uint32_t)(T.t[e + 3] >> 32)));
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < KMAX; ++e) {
+          if (e >= KMAX - k) {
+            oi[e - (KMAX - k)] = (int32_t)(uint32_t)(T.t[e] & 0xffffffffull) - 1;
+            od[e - (KMAX - k)] = __uint_as_float((uint32_t)(T.t[e] >> 32));
+          }
         }
       }
     }
@@ -1164,9 +1176,13 @@ void l2l_knn(const Layout& L, char* ws, int k, int k_row, int col0, int pass, fl
   const float4* src = sets ? at<float4>(ws, L.pts2) : at<float4>(ws, L.pts);
   const float4* qry = sets ? src + L.n_src : src;
   const uint2* qrange = sets ? at<uint2>(ws, L.qrange) : nullptr;
+  // 16-byte row stores need 16-byte aligned outputs and rows of a multiple of 4 entries
+  // (col0 is a multiple of 32)
+  const int vec_out = ((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(d2)) & 15u) == 0 &&
+                      (k_row % 4) == 0;
   k_l2l_knn<KMAX, PER, LB><<<sms * 8, 32 * kL2LWarps, smem, s>>>(
       src, at<NodeRec>(ws, L.nodes[0]), at<uint2>(ws, L.ilo[0]), at<IEntry>(ws, L.arena), k, k_row, col0,
-      kCtrWalk + pass, qry, qrange, pl, order, idx, d2, m); note_launch();
+      kCtrWalk + pass, qry, qrange, vec_out, pl, order, idx, d2, m); note_launch();
 }
 
 template <bool PER>
