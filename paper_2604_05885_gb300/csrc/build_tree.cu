@@ -256,15 +256,22 @@ __device__ __forceinline__ uint64_t morton(float x, float y, float z, const floa
 }
 
 // Histogram of all radix digits of the keys held by a warp (lanes with
-// valid=false contribute nothing); warp-aggregated shared-memory increments.
+// valid=false contribute nothing).  A digit shared by the whole warp (the high
+// digits of spatially coherent input) is added once; otherwise every lane adds
+// its own (shared-memory atomics resolve the few collisions of random digits).
 __device__ __forceinline__ void hist_key(uint32_t (*sh)[kRadixBins], uint64_t key, bool valid) {
   const unsigned act = __ballot_sync(0xffffffffu, valid);
   if (!valid) return;
 #pragma unroll
+  const int leader = __ffs(act) - 1;
   for (int p = 0; p < kRadixPasses; ++p) {
     uint32_t d = (uint32_t)(key >> (p * kRadixBits)) & (kRadixBins - 1);
-    unsigned peers = __match_any_sync(act, d);
-    if ((int)(__ffs(peers) - 1) == lane_id()) atomicAdd(&sh[p][d], (uint32_t)__popc(peers));
+    const uint32_t d0 = __shfl_sync(act, d, leader);
+    if (__all_sync(act, d == d0)) {
+      if (lane_id() == leader) atomicAdd(&sh[p][d], (uint32_t)__popc(act));
+    } else {
+      atomicAdd(&sh[p][d], 1u);
+    }
   }
 }
 
@@ -1097,10 +1104,12 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
   // node records
   k_leaf_nodes<<<grid_for((L.cap_nodes[0]) * 32, 256, sms * 16), 256, 0, s>>>(
       pts, at<int32_t>(ws, L.spl[0]), at<NodeRec>(ws, L.nodes[0]), m); note_launch();
-  for (int p = 1; p < L.n_planes; ++p)
+  for (int p = 1; p < L.n_planes; ++p) {
     k_upper_nodes<<<grid_for(L.cap_nodes[p] * 32, 256, sms * 16), 256, 0, s>>>(
         at<int32_t>(ws, L.spl[p]), at<int32_t>(ws, L.gap[p]), at<NodeRec>(ws, L.nodes[p - 1]),
-        at<NodeRec>(ws, L.nodes[p]), p, m); note_launch();
+        at<NodeRec>(ws, L.nodes[p]), p, m);
+    note_launch();
+  }
   if (n_b > 0) {
     // split the sorted points by type; leaves get source ranges and query ranges,
     // node counts become source counts
