@@ -643,6 +643,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const uint64_t* _
                                                                Meta* m) {
   __shared__ uint64_t s_key[kScanTile + 2 * 32 + 1];
   __shared__ int8_t s_w[kScanTile + 32];
+  __shared__ int8_t s_pre[kScanTile + 32], s_suf[kScanTile + 32];
   __shared__ uint32_t s_tile;
   const int reg_lvl = m->reg_lvl[0];
   if (threadIdx.x == 0) s_tile = atomicAdd(&m->tile_ctr[kCtrLeafSplits], 1u);
@@ -665,6 +666,23 @@ __global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const uint64_t* _
     s_w[t] = (int8_t)v;
   }
   __syncthreads();
+  // sliding minimum of width M over s_w: per block of M slots (aligned at 0),
+  // prefix and suffix minima; the window [u, u + M - 1] meets at most two blocks
+  const int nw = kScanTile + M;
+  for (int b0 = threadIdx.x * M; b0 < nw; b0 += kSplitThreads * M) {
+    const int b1 = min(b0 + M, nw);
+    int8_t run = 127;
+    for (int t = b0; t < b1; ++t) {
+      run = min(run, s_w[t]);
+      s_pre[t] = run;
+    }
+    run = 127;
+    for (int t = b1 - 1; t >= b0; --t) {
+      run = min(run, s_w[t]);
+      s_suf[t] = run;
+    }
+  }
+  __syncthreads();
   uint32_t flags = 0;
   int cnt = 0;
 #pragma unroll
@@ -677,13 +695,11 @@ __global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const uint64_t* _
       int li = (int)(i - k0);  // s_key index of point i
       int g = level_ext(s_key[li - 1], s_key[li], i - 1, i);
       f = g > reg_lvl;  // regularisation (Sec. II-D); reg_lvl = 127 when off
-      int64_t jlo = f ? 1 : max64(0, i - M), jhi = f ? 0 : min64(i - 1, n - 1 - M);
-      for (int64_t j = jlo; j <= jhi; ++j) {
-        if (s_w[j - k0] <= g) {
-          f = true;
-          break;
-        }
-      }
+      // windows j in [i - M, i - 1] (slots u .. u + M - 1, u = i - g0; slots of
+      // invalid j hold 127): split when the smallest window level is <= g
+      const int u = (int)(i - g0);
+      const int wmin = min((int)s_suf[u], (int)s_pre[u + M - 1]);
+      f = f || wmin <= g;
     }
     flags |= (uint32_t)f << r;
     cnt += f;
