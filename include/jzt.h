@@ -260,6 +260,16 @@ int jzt_batch_run(const jzt_job *jobs, int n_jobs, const jzt_params *p,
 int jzt_knn_noalloc(const float *d_xyz, int64_t n, int k, float periodic_L,
                     int32_t *d_idx, float *d_dist2, void *stream, jzt_status_info *info);
 
+/* Failure-path self-test (no counterpart in the paper): makes one of the library's
+ * bounded waits run out -- which = 0: an mbarrier phase that never completes (the
+ * LeafToLeaf staging wait), 1: a published word that nobody sets (the radix-sort
+ * look-back poll) -- after `limit` polls (1..2^26), then synchronises `stream` and
+ * returns the status like jzt_status: JZT_ERR_TIMEOUT when the wait gave up.  The
+ * context stays usable.  d_ws: any workspace of at least jzt_workspace_bytes(1, 0)
+ * bytes (its status block is overwritten). */
+int jzt_selftest_wait(int which, long long limit, void *d_ws, size_t ws_bytes, void *stream,
+                      jzt_status_info *info);
+
 /* Instrumentation (no counterpart in the paper; used to measure the kernels).
  * jzt_profile_enable(1) makes every later call record a CUDA event pair on its
  * own stream around each kernel phase (phase names: jzt_profile_phase_name).

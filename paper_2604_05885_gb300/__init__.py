@@ -42,7 +42,7 @@ SYMBOLS = ("jzt_workspace_bytes", "jzt_build", "jzt_tree_knn", "jzt_tree_fof", "
            "jzt_status", "jzt_tree_arrays", "jzt_tree_plane", "jzt_tree_free", "jzt_last_error",
            "jzt_version", "jzt_profile_enable", "jzt_profile_read", "jzt_profile_phase_name",
            "jzt_knn_noalloc", "jzt_batch_run", "jzt_workspace_bytes_query", "jzt_build_query",
-           "jzt_knn_query", "jzt_tree_fof_catalogue")
+           "jzt_knn_query", "jzt_tree_fof_catalogue", "jzt_selftest_wait")
 JZT_OP_KNN = 0
 JZT_OP_FOF = 1
 
@@ -109,6 +109,8 @@ def _load():
     lib.jzt_build_query.argtypes = [vp, i64, vp, i64, f32, ctypes.POINTER(Params), vp, sz, vp, ctypes.POINTER(vp)]
     lib.jzt_knn_query.argtypes = [vp, i64, vp, i64, ctypes.c_int, f32, vp, vp, vp, sz, vp]
     lib.jzt_tree_fof_catalogue.argtypes = [vp, f32, vp, ctypes.c_int, f32, vp, vp, vp, i64, vp, vp]
+    lib.jzt_selftest_wait.argtypes = [ctypes.c_int, ctypes.c_longlong, vp, sz, vp, ctypes.POINTER(StatusInfo)]
+    lib.jzt_selftest_wait.restype = ctypes.c_int
     for name in ("jzt_workspace_bytes_query", "jzt_build_query", "jzt_knn_query", "jzt_tree_fof_catalogue"):
         getattr(lib, name).restype = ctypes.c_int
     lib.jzt_tree_free.argtypes = [vp]

@@ -355,6 +355,23 @@ int jzt_tree_fof_catalogue(jzt_tree* t, float b, const float* d_vel, int min_cou
   return JZT_OK;
 }
 
+int jzt_selftest_wait(int which, long long limit, void* d_ws, size_t ws_bytes, void* stream, jzt_status_info* info) {
+  if (which != 0 && which != 1) return fail(JZT_ERR_INVALID, "which must be 0 (mbarrier) or 1 (flag)");
+  if (limit < 1 || limit > (1ll << 26)) return fail(JZT_ERR_INVALID, "limit must be in 1..2^26");
+  if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255u)) return fail(JZT_ERR_INVALID, "bad workspace");
+  Params P;
+  const char* why = nullptr;
+  if (int e = resolve_params(nullptr, &P, &why)) return fail(e, why);
+  Layout L;
+  compute_layout(1, P, 0, ws_bytes, &L);
+  if (L.cap_ilist < 0) return fail(JZT_ERR_WORKSPACE, "workspace too small");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  launch_selftest_wait(L, static_cast<char*>(d_ws), which, limit, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "jzt_selftest_wait launch");
+  return jzt_status(d_ws, stream, info);
+}
+
 int jzt_knn_query(const float* d_src, int64_t n_src, const float* d_qry, int64_t n_qry, int k, float periodic_L,
                   int32_t* d_idx, float* d_dist2, void* d_ws, size_t ws_bytes, void* stream) {
   if (k < 1 || k > kMaxKTotal || (int64_t)k > n_src) {

@@ -164,6 +164,7 @@ void launch_fof(const Layout& L, char* ws, float periodic_L, float b, int32_t* d
                 cudaStream_t s);
 // shared (build_tree.cu)
 void launch_super_level(const Layout& L, char* ws, cudaStream_t s);
+void launch_selftest_wait(const Layout& L, char* ws, int which, long long limit, cudaStream_t s);
 size_t catalogue_scratch_bytes(int64_t n);
 int launch_catalogue(const Layout& L, char* ws, float periodic_L, const float* d_vel, int min_count,
                      float particle_mass, int32_t* d_order, jzt_group* d_groups, int64_t cap_groups,

@@ -174,10 +174,14 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 // Bounded wait on a barrier phase; false when the budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; ++it)
+// Bounded wait for the phase `parity` of an mbarrier: false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, long long limit) {
+  for (long long it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_n(bar, parity, kSpinLimit);
 }
 
 constexpr int kN2NWarps = 4;
@@ -1232,6 +1236,48 @@ void knn_all(const Layout& L, char* ws, float pl, int k, int order, int32_t* idx
 }
 
 }  // namespace
+
+namespace {
+
+__global__ void k_selftest_reset(Meta* m, uint32_t* flag) {
+  if (threadIdx.x == 0) {
+    m->status = 0;
+    m->detail = 0;
+    *flag = 0;
+  }
+}
+
+// Failure-path self-test: the bounded waits of the walk and the sort, made to
+// run out -- an mbarrier phase that never completes (nobody arrives) and a
+// published-word flag that nobody sets.  Both must end with JZT_ERR_TIMEOUT in
+// the status word and leave the context usable.
+__global__ void k_selftest_wait(int which, long long limit, const uint32_t* flag, Meta* m) {
+  __shared__ uint64_t bar;
+  const int lane = lane_id();
+  if (lane == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (which == 0) {
+    const bool ok = __all_sync(kFull, mbar_wait_n(&bar, 0u, limit));
+    if (!ok && lane == 0) set_error(m, JZT_ERR_TIMEOUT, kStageLeaf);
+  } else if (lane == 0) {
+    long long it = 0;
+    while (ld_relaxed_u32(flag) == 0u && ++it < limit) {
+    }
+    if (it >= limit) set_error(m, JZT_ERR_TIMEOUT, kStageSort);
+  }
+}
+
+}  // namespace
+
+void launch_selftest_wait(const Layout& L, char* ws, int which, long long limit, cudaStream_t s) {
+  Meta* m = at<Meta>(ws, L.meta);
+  uint32_t* flag = at<uint32_t>(ws, L.arena);
+  k_selftest_reset<<<1, 32, 0, s>>>(m, flag); note_launch();
+  k_selftest_wait<<<1, 32, 0, s>>>(which, limit, flag, m); note_launch();
+}
 
 void launch_knn(const Layout& L, char* ws, float periodic_L, int k, int order, int32_t* d_idx,
                 float* d_d2, cudaStream_t s) {
