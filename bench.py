@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--cpu-side", type=float, default=0.75,
                     help="side of the sub-cube of the workload timed on the CPU")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kdtree-side", type=float, default=0.5,
+                    help="side of the sub-cube timed with scipy's k-d tree (context)")
     ap.add_argument("--nmax0", type=int, default=0, help="leaf capacity (0 = library default)")
     ap.add_argument("--cache", default=os.path.join(tempfile.gettempdir(), "jzt_bench_cache"))
     ap.add_argument("--batch-sets", type=int, default=512, help="batched sets (0 = skip the batched run)")
@@ -307,6 +309,26 @@ def serving_run(a, dev, log):
             "load_sweep": sweep or None}
 
 
+def cpu_kdtree(x, n_side, k, side):
+    """Context only: scipy's multithreaded k-d tree (build + kNN query, all host
+    cores) on the points of the sub-cube [0, side)^3, treated as an open box."""
+    import numpy as np
+    try:
+        from scipy.spatial import cKDTree
+    except ImportError as exc:  # pragma: no cover
+        return {"unavailable": str(exc)}
+    sel = np.all(x < np.float32(side), axis=1)
+    xs = np.ascontiguousarray(x[sel], dtype=np.float64)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    tr = cKDTree(xs)
+    tr.query(xs, k, workers=-1)
+    dt = time.perf_counter() - t0
+    return {"value": xs.shape[0] / dt, "unit": UNIT, "cores": cores, "kind": "scipy cKDTree (kNN only)",
+            "sample": f"{xs.shape[0]} points of the sub-cube [0,{side})^3 of the {n_side}^3 Zel'dovich set, "
+                      f"open box; build + query k={k}", "seconds": dt}
+
+
 def dist_env():
     """(rank, world size, local rank) from the torchrun environment (1 process: 0, 1, 0)."""
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
@@ -432,6 +454,28 @@ def main():
     st = tree.status(raise_on_error=True)
     ms_step = max_over_ranks([ms_total / a.steps], dist, dev)[0]
     value = whole_job_rate(n, world, ms_step)
+
+    # kNN with rows in z order (Sec. III-G's benchmark output, no final reordering):
+    # build + kNN, compared with the same in input order
+    zo = {}
+    for order in (1, 0):
+        def knn_step():
+            t3 = jzt.build(x_dev, periodic_L=L, workspace=ws, params=params)
+            t3.knn(k, order=order, out=(idx, d2))
+            return t3
+        t3 = knn_step()
+        z0 = torch.cuda.Event(enable_timing=True)
+        z1 = torch.cuda.Event(enable_timing=True)
+        z0.record(stream)
+        for _ in range(3):
+            t3 = knn_step()
+        z1.record(stream)
+        torch.cuda.synchronize(dev)
+        t3.status(raise_on_error=True)
+        zms = z0.elapsed_time(z1) / 3
+        zo["z_order" if order else "input_order"] = {"ms_per_step": zms, "value": n / (zms / 1000.0), "unit": UNIT}
+    del t3
+    jzt.profile_read()
 
     # FoF catalogue (Sec. IV-B): build + FoF + group order + reductions, groups >= 20
     cat = None
@@ -577,7 +621,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "clocks": clk, "e2e": e2e, "e2e_serial": e2e_serial, "gpu_launches": launches,
-            "fof_catalogue": cat, "roofline": roofline,
+            "fof_catalogue": cat, "knn_build_plus_walk": zo, "roofline": roofline,
             "roofline_sort": roof_sort, "roofline_build": roof_build,
             "phases_ms_per_step": {ph: phase_ms[ph] / steps for ph in phase_ms},
             "knn_particles_per_s": n / ((build_ms + knn_ms) / 1000.0) if knn_ms else None,
@@ -606,6 +650,7 @@ def main():
                                    "arrival_rate_per_s": sv["arrival_rate_per_s"]}
     if rank == 0 and not a.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(x, n_side, k, b, a.cpu_side)
+        line["cpu_kdtree"] = cpu_kdtree(x, n_side, k, a.kdtree_side)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
