@@ -275,25 +275,35 @@ __global__ void __launch_bounds__(128) k_l2l_fof(const float4* __restrict__ pts,
       const bool act = ia < A.count;
       const int a = A.first + ia;
       const float4 pa = act ? pts[a] : make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int jb = self ? a0 : 0; jb < B.count; ++jb) {
-        const int bb = B.first + jb;
-        if (!act || (self && bb <= a)) continue;
-        const float4 pb = __ldg(pts + bb);
-        float dx = pb.x - pa.x, dy = pb.y - pa.y, dz = pb.z - pa.z;
-        if (PER) {
-          if (ambiguous) {
-            dx = wrap1(dx, L, invL);
-            dy = wrap1(dy, L, invL);
-            dz = wrap1(dz, L, invL);
-          } else {
-            dx = __fadd_rn(dx, sh[0]);
-            dy = __fadd_rn(dy, sh[1]);
-            dz = __fadd_rn(dz, sh[2]);
+      // four source points per step: independent loads, the union only on a hit
+      constexpr int U = 4;
+      for (int jb0 = self ? a0 : 0; jb0 < B.count; jb0 += U) {
+        float d2[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int jb = jb0 + u;
+          const float4 pb = __ldg(pts + B.first + (jb < B.count ? jb : B.count - 1));
+          float dx = pb.x - pa.x, dy = pb.y - pa.y, dz = pb.z - pa.z;
+          if (PER) {
+            if (ambiguous) {
+              dx = wrap1(dx, L, invL);
+              dy = wrap1(dy, L, invL);
+              dz = wrap1(dz, L, invL);
+            } else {
+              dx = __fadd_rn(dx, sh[0]);
+              dy = __fadd_rn(dy, sh[1]);
+              dz = __fadd_rn(dz, sh[2]);
+            }
           }
+          d2[u] = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+          const int bb = B.first + jb;
+          if (!act || jb >= B.count || (self && bb <= a)) d2[u] = INFINITY;
         }
-        const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-        if (d2 <= b2) {
-          if (!uf_union(ig_pt, a, bb)) union_fail = true;
+        const bool any = d2[0] <= b2 || d2[1] <= b2 || d2[2] <= b2 || d2[3] <= b2;
+        if (any) {
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (d2[u] <= b2 && !uf_union(ig_pt, a, B.first + jb0 + u)) union_fail = true;
         }
       }
     }
