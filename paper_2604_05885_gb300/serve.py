@@ -48,7 +48,9 @@ class Request:
     hit: bool = False
     result: object = None
     lane: int = -1
-    _event: object = field(default=None, repr=False)
+    _event: object = field(default=None, repr=False)  # completion event of the request's work
+    _res: object = field(default=None, repr=False)    # the resident tree it runs on
+    _pts: object = field(default=None, repr=False)    # its points, while a build needs them
 
 
 def _out_bytes(r: Request) -> int:
