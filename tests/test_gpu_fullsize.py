@@ -71,3 +71,14 @@ def test_clustered_2_24():
     w, x = workloads.config_clustered_16m()
     idx, d2, lab = _run(x, w.k, w.b, w.periodic_L)
     _check(x, w.k, w.b, w.periodic_L, idx, d2, lab, 20000, 8)
+
+
+def test_cell_oracle_matches_brute_force_at_full_size():
+    """The cell-list kNN oracle used above, checked against all-pairs brute force on
+    1000 seeded sampled queries of the 2^27-point set (exact rows, including ties)."""
+    x = _zeldovich512()
+    q = np.sort(np.random.default_rng(9).choice(x.shape[0], 1000, replace=False))
+    ci, cd = oracle.knn_cells(x, 16, 1.0, queries=q)
+    bi, bd = oracle.knn_brute(x, 16, 1.0, queries=q)
+    assert np.array_equal(ci, bi)
+    assert np.array_equal(cd, bd)
