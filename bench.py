@@ -639,9 +639,10 @@ def main():
     def log(msg):
         print(f"[bench] {msg}", file=sys.stderr, flush=True)
 
-    if a.batch_sets > 0:
+    # the batched and serving runs describe one GPU; replicas (N > 1) skip them
+    if a.batch_sets > 0 and world == 1:
         line["batched"] = batched_run(a, dev, log)
-    if a.serve_requests > 0:
+    if a.serve_requests > 0 and world == 1:
         sv = serving_run(a, dev, log)
         line["serving"] = sv
         line["p50_p99_latency"] = {"p50_ms": sv["served"]["p50_ms"], "p99_ms": sv["served"]["p99_ms"],
