@@ -635,7 +635,9 @@ __device__ __forceinline__ float point_box_d2(float4 q, const NodeRec& b, float 
 #define JZT_L2L_STAGES 4
 #endif
 #ifndef JZT_L2L_MINBLOCKS
-#define JZT_L2L_MINBLOCKS(kmax) 1
+// blocks per SM: 4 caps registers at 128, 3 at 168 (neither spills); shared
+// memory allows 4 blocks at KMAX <= 16 and 3 at KMAX = 32
+#define JZT_L2L_MINBLOCKS(kmax) ((kmax) <= 16 ? 4 : 3)
 #endif
 constexpr int kQF = JZT_L2L_QF;          // buffered candidates per lane between threshold updates
 constexpr int kL2LWarps = 4;
@@ -647,12 +649,13 @@ constexpr int kStages = JZT_L2L_STAGES;  // source leaves in flight per warp
 constexpr unsigned long long kKeyInf = ~0ull;
 
 // Per-warp shared memory: staged source leaves and, per lane, a buffer of
-// candidate (d2 bits, original index) pairs.  The buffer holds KMAX + 32
-// entries, so that after an exact compaction to k entries a full source leaf
-// always fits.
+// candidate (d2 bits, original index) pairs.  The buffer holds KMAX + 16
+// entries: a compaction leaves at most KMAX, and the scan compacts as soon as
+// more than kCap - 8 are held after a window of 8 source points, so the next
+// window always fits.  At KMAX <= 16 four blocks of four warps fit one SM.
 template <int KMAX>
 struct __align__(16) L2LWarpSmem {
-  static constexpr int kCap = KMAX + 32;
+  static constexpr int kCap = KMAX + 16;
   float4 pts[kStages][32];  // staged source leaves (<= 32 points each)
   float4 meta[32][3];       // list entries of the current batch (see k_l2l_knn)
   uint64_t bar[kStages];
@@ -763,10 +766,10 @@ __device__ __forceinline__ void select_exact(uint2 (*buf)[32], int nb, int k, in
   }
 }
 
-// Keep only the buffer entries at or below thr.  If a lane still holds too many
-// (exact ties at the k-th distance), every lane also drops the tied entries
-// beyond its k best: fewer than k entries lie below thr, and of those at thr
-// the ones with the smallest indices are kept (indices are distinct).
+// Keep only the buffer entries at or below thr.  If a lane still holds more
+// than KMAX (exact ties at the k-th distance), every lane also drops the tied
+// entries beyond its k best: fewer than k entries lie below thr, and of those
+// at thr the ones with the smallest indices are kept (indices are distinct).
 template <int KMAX>
 __device__ __forceinline__ void compact(uint2 (*buf)[32], Cand<KMAX>& C, int k, int lane) {
   int w = 0;
@@ -775,7 +778,7 @@ __device__ __forceinline__ void compact(uint2 (*buf)[32], Cand<KMAX>& C, int k, 
     if (__uint_as_float(e.x) <= C.thr) buf[w++][lane] = e;
   }
   C.nb = C.nm = w;
-  if (!__any_sync(kFull, C.nb > L2LWarpSmem<KMAX>::kCap - 16)) return;
+  if (!__any_sync(kFull, C.nb > KMAX)) return;
   const uint32_t tb = __float_as_uint(C.thr);
   int less = 0;
   for (int r = 0; r < C.nb; ++r) less += __uint_as_float(buf[r][lane].x) < C.thr ? 1 : 0;
@@ -888,15 +891,15 @@ __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt
     for (int u = 1; u < W; ++u) mn = fminf(mn, d2[u]);
     if (__any_sync(kFull, mn <= C.thr)) {
       // at a window's start C.nb <= kCap - W (the check below compacts
-      // otherwise), so the W slots from C.nb on are inside the buffer.  Every
-      // distance is written to slot C.nb and kept only if it passes (no
-      // divergent branch per source point); a rejected one is overwritten.
+      // otherwise), so the W slots from C.nb on are inside the buffer
 #pragma unroll
       for (int u = 0; u < W; ++u) {
-        buf[C.nb][lane] = make_uint2(__float_as_uint(d2[u]), (uint32_t)id[u]);
         bool keep = d2[u] <= C.thr;
         if (LB) keep = keep && (d2[u] > lb_d2 || (d2[u] == lb_d2 && id[u] > lb_id));
-        C.nb += keep ? 1 : 0;
+        if (keep) {
+          buf[C.nb][lane] = make_uint2(__float_as_uint(d2[u]), (uint32_t)id[u]);
+          ++C.nb;
+        }
       }
       if (__any_sync(kFull, C.nb - C.nm > kQF - W || C.nb > kCap - W)) {
         if (C.nb > kCap) set_error(m, JZT_ERR_INTERNAL, kStageLeaf);  // cannot happen
