@@ -632,12 +632,13 @@ __device__ __forceinline__ float point_box_d2(float4 q, const NodeRec& b, float 
 #define JZT_L2L_QF 16
 #endif
 #ifndef JZT_L2L_STAGES
-#define JZT_L2L_STAGES 4
+#define JZT_L2L_STAGES 2
 #endif
 #ifndef JZT_L2L_MINBLOCKS
-// blocks per SM: 4 caps registers at 128, 3 at 168 (neither spills); shared
-// memory allows 4 blocks at KMAX <= 16 and 3 at KMAX = 32
-#define JZT_L2L_MINBLOCKS(kmax) ((kmax) <= 16 ? 4 : 3)
+// blocks per SM: 5 caps registers at 96 (a few spilled words, faster than 4
+// blocks without spills), 3 at 168; shared memory allows 5 blocks at
+// KMAX <= 16 (two staged leaves per warp) and 3 at KMAX = 32
+#define JZT_L2L_MINBLOCKS(kmax) ((kmax) <= 16 ? 5 : 3)
 #endif
 constexpr int kQF = JZT_L2L_QF;          // buffered candidates per lane between threshold updates
 constexpr int kL2LWarps = 4;
@@ -652,7 +653,7 @@ constexpr unsigned long long kKeyInf = ~0ull;
 // candidate (d2 bits, original index) pairs.  The buffer holds KMAX + 16
 // entries: a compaction leaves at most KMAX, and the scan compacts as soon as
 // more than kCap - 8 are held after a window of 8 source points, so the next
-// window always fits.  At KMAX <= 16 four blocks of four warps fit one SM.
+// window always fits.
 template <int KMAX>
 struct __align__(16) L2LWarpSmem {
   static constexpr int kCap = KMAX + 16;
