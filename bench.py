@@ -364,6 +364,47 @@ def whole_job_rate(units_per_rank, world, ms_max):
     return world * units_per_rank / (ms_max / 1000.0)
 
 
+def catalogue_timing(x_dev, L, b, params, ws, lab, stream, dev, reps=3):
+    """Build + FoF + catalogue (groups of at least 20 members) through
+    jzt_tree_fof_catalogue, timed with CUDA events over ``reps`` calls."""
+    import torch
+
+    import paper_2604_05885_gb300 as jzt
+    n = int(x_dev.shape[0])
+    try:
+        cap = n // 20 + 1
+        order_c = torch.empty(n, dtype=torch.int32, device=dev)
+        gbuf = torch.empty(cap * jzt.GROUP_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        ng = torch.zeros(1, dtype=torch.int64, device=dev)
+
+        def cat_step():
+            t2 = jzt.build(x_dev, periodic_L=L, workspace=ws, params=params)
+            rc = jzt.lib.jzt_tree_fof_catalogue(t2._h, float(b), None, 20, 1.0, ctypes.c_void_p(lab.data_ptr()),
+                                                ctypes.c_void_p(order_c.data_ptr()), ctypes.c_void_p(gbuf.data_ptr()),
+                                                cap, ctypes.c_void_p(ng.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+            if rc != 0:
+                raise RuntimeError(f"jzt_tree_fof_catalogue: {rc} {jzt.lib.jzt_last_error().decode()}")
+            return t2
+        t2 = cat_step()
+        t2.status(raise_on_error=True)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(reps):
+            t2 = cat_step()
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        t2.status(raise_on_error=True)
+        ms_cat = c0.elapsed_time(c1) / reps
+        out = {"ms_per_step": ms_cat, "value": n / (ms_cat / 1000.0), "unit": UNIT, "n": n, "min_count": 20,
+               "groups": int(ng.item()), "step": "build + FoF + group order + catalogue reduction"}
+        del order_c, gbuf, ng, t2
+    except Exception as exc:  # noqa: BLE001  (reported, not fatal for the main line)
+        out = {"error": str(exc)[:200]}
+    jzt.profile_read()
+    return out
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -406,6 +447,7 @@ def main():
     import torch
 
     import paper_2604_05885_gb300 as jzt
+    import workloads
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -477,36 +519,18 @@ def main():
     del t3
     jzt.profile_read()
 
-    # FoF catalogue (Sec. IV-B): build + FoF + group order + reductions, groups >= 20
-    cat = None
+    # FoF catalogue (Sec. IV-B): build + FoF + group order + reductions, groups >= 20; on the
+    # benchmark set (all singletons at b = 0.2 spacings) and on the 2^24 clustered periodic set
+    cat = catalogue_timing(x_dev, L, b, params, ws, lab, stream, dev)
     try:
-        cap = n // 20 + 1
-        order_c = torch.empty(n, dtype=torch.int32, device=dev)
-        gbuf = torch.empty(cap * jzt.GROUP_DTYPE.itemsize, dtype=torch.uint8, device=dev)
-        ng = torch.zeros(1, dtype=torch.int64, device=dev)
-
-        def cat_step():
-            t2 = jzt.build(x_dev, periodic_L=L, workspace=ws, params=params)
-            jzt.lib.jzt_tree_fof_catalogue(t2._h, float(b), None, 20, 1.0, ctypes.c_void_p(lab.data_ptr()),
-                                           ctypes.c_void_p(order_c.data_ptr()), ctypes.c_void_p(gbuf.data_ptr()),
-                                           cap, ctypes.c_void_p(ng.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
-            return t2
-        t2 = cat_step()
-        t2.status(raise_on_error=True)
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        for _ in range(3):
-            t2 = cat_step()
-        c1.record(stream)
-        torch.cuda.synchronize(dev)
-        t2.status(raise_on_error=True)
-        ms_cat = c0.elapsed_time(c1) / 3
-        cat = {"ms_per_step": ms_cat, "value": n / (ms_cat / 1000.0), "unit": UNIT, "min_count": 20,
-               "groups": int(ng.item()), "step": "build + FoF + group order + catalogue reduction"}
-        del order_c, gbuf, ng, t2
+        xc = torch.from_numpy(workloads.clustered(1 << 24, 2)).to(dev)
+        wsc = jzt.alloc_workspace(xc.shape[0], 0, params, dev)
+        labc = torch.empty(xc.shape[0], dtype=torch.int32, device=dev)
+        cat_c = catalogue_timing(xc, 1.0, 0.2 / 256, params, wsc, labc, stream, dev)
+        cat_c["workload"] = "clustered 2^24, periodic, seed 2, b = 0.2/256"
+        del xc, wsc, labc
     except Exception as exc:  # noqa: BLE001  (reported, not fatal for the main line)
-        cat = {"error": str(exc)[:200]}
+        cat_c = {"error": str(exc)[:200]}
     jzt.profile_read()
 
     del ws, idx, d2, lab, tree
@@ -621,7 +645,7 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "clocks": clk, "e2e": e2e, "e2e_serial": e2e_serial, "gpu_launches": launches,
-            "fof_catalogue": cat, "knn_build_plus_walk": zo, "roofline": roofline,
+            "fof_catalogue": cat, "fof_catalogue_clustered": cat_c, "knn_build_plus_walk": zo, "roofline": roofline,
             "roofline_sort": roof_sort, "roofline_build": roof_build,
             "phases_ms_per_step": {ph: phase_ms[ph] / steps for ph in phase_ms},
             "knn_particles_per_s": n / ((build_ms + knn_ms) / 1000.0) if knn_ms else None,
