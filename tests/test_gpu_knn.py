@@ -57,6 +57,19 @@ def test_lattice_ties_by_index():
         assert np.array_equal(idx, ri)  # ties are exact in float32: indices must agree
 
 
+@pytest.mark.parametrize("k", [2, 5, 10, 20, 30])
+def test_lattice_ties_by_index_small_k(k):
+    """Rows ending inside a shell of equal distances (6 at h, 12 at sqrt(2) h, 8 at
+    sqrt(3) h around the point itself) under every candidate-list size (4, 8, 16,
+    32): the tied entries kept are those with the lowest indices."""
+    import paper_2604_05885_gb300 as jzt
+    for L, xs in ((0.0, workloads.lattice(9, spacing_bits=9)), (1.0, workloads.lattice(12, spacing_bits=4))):
+        tree = jzt.build(to_dev(xs), periodic_L=L)
+        idx, _ = knn_parity(tree, xs, k, L)
+        ri, _ = oracle.knn_brute(xs, k, L)
+        assert np.array_equal(idx, ri)
+
+
 def test_duplicates_and_degenerate_geometry():
     import paper_2604_05885_gb300 as jzt
     x = workloads.uniform(2000, 12)
