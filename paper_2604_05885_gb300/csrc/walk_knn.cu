@@ -628,9 +628,6 @@ __device__ __forceinline__ float point_box_d2(float4 q, const NodeRec& b, float 
   return s * kLowSlack;
 }
 
-#ifndef JZT_L2L_QF
-#define JZT_L2L_QF 16
-#endif
 #ifndef JZT_L2L_STAGES
 #define JZT_L2L_STAGES 2
 #endif
@@ -640,7 +637,12 @@ __device__ __forceinline__ float point_box_d2(float4 q, const NodeRec& b, float 
 // KMAX <= 16 (two staged leaves per warp) and 3 at KMAX = 32
 #define JZT_L2L_MINBLOCKS(kmax) ((kmax) <= 16 ? 5 : 3)
 #endif
-constexpr int kQF = JZT_L2L_QF;          // buffered candidates per lane between threshold updates
+// Threshold updates: once a lane holds kMergeAt unmerged candidates, its oldest
+// kMergeBatch are merged into the distance list.  Batches of 8 halve the sorting
+// network at KMAX <= 16; at KMAX = 32 the list's own merge network dominates and
+// batches of 16, merged as soon as 9 are waiting, are faster.
+template <int KMAX> constexpr int kMergeBatch = KMAX <= 16 ? 8 : 16;
+template <int KMAX> constexpr int kMergeAt = KMAX <= 16 ? 8 : 9;
 constexpr int kL2LWarps = 4;
 constexpr int kStages = JZT_L2L_STAGES;  // source leaves in flight per warp
 
@@ -730,20 +732,23 @@ struct Cand {
   uint32_t pushed;
 };
 
-// Merge the unmerged buffer entries (at most kQF) into F; returns the new thr.
+// Merge the oldest unmerged buffer entries (at most kMergeBatch) into F and
+// update thr.
 template <int KMAX>
 __device__ __forceinline__ void merge_distances(uint2 (*buf)[32], Cand<KMAX>& C, int lane, bool act) {
   constexpr int kCap = L2LWarpSmem<KMAX>::kCap;
-  float b[kQF];
+  constexpr int B = kMergeBatch<KMAX>;
+  const int take = min(B, C.nb - C.nm);
+  float b[B];
 #pragma unroll
-  for (int t = 0; t < kQF; ++t) {
-    const int r = C.nm + t < C.nb ? C.nm + t : 0;  // index stays inside the lane's buffer
+  for (int t = 0; t < B; ++t) {
+    const int r = t < take ? C.nm + t : 0;  // index stays inside the lane's buffer
     const float v = __uint_as_float(buf[r < kCap ? r : 0][lane].x);
-    b[t] = C.nm + t < C.nb ? v : INFINITY;
+    b[t] = t < take ? v : INFINITY;
   }
-  C.pushed += (uint32_t)(C.nb - C.nm);
-  C.nm = C.nb;
-  C.F.template merge<kQF>(b);
+  C.pushed += (uint32_t)take;
+  C.nm += take;
+  C.F.template merge<B>(b);
   C.thr = act ? C.F.t[KMAX - 1] : -INFINITY;
 }
 
@@ -871,8 +876,11 @@ __device__ __forceinline__ void window_d2(const float4* __restrict__ sp, int j0,
 
 // Scan one staged source leaf: every (query lane, source point) pair; points at
 // or below the lane's running k-th distance are appended to its buffer, and the
-// distance list (hence thr) is updated once a lane has more than kQF - W
-// unmerged entries.  One copy of the candidate code serves every image mode.
+// distance list (hence thr) is updated with the oldest kMergeBatch entries once
+// a lane has kMergeAt unmerged ones, so that between windows every lane holds
+// fewer than kMergeAt (a window adds at most W <= kMergeBatch).  Before a
+// compaction every entry is merged: thr is then the k-th smallest distance of
+// the whole buffer.  One copy of the candidate code serves every image mode.
 template <bool PER, bool LB, int KMAX>
 __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt, int G, int sub, int mode,
                                           const float4& qp, const float* sh, float L, float invL,
@@ -880,7 +888,8 @@ __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt
                                           float lb_d2, int lb_id, Meta* m) {
   constexpr int kCap = L2LWarpSmem<KMAX>::kCap;
   constexpr int W = 8;
-  static_assert(kQF >= W, "a window's candidates must fit the merge batch");
+  static_assert(kMergeBatch<KMAX> >= W && kMergeAt<KMAX> - 1 <= kMergeBatch<KMAX>,
+                "one merge must bring every lane below kMergeAt, a second one to zero");
   for (int j0 = 0; j0 < cnt; j0 += W * G) {
     float d2[W];
     int id[W];
@@ -902,10 +911,13 @@ __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt
           ++C.nb;
         }
       }
-      if (__any_sync(kFull, C.nb - C.nm > kQF - W || C.nb > kCap - W)) {
+      if (__any_sync(kFull, C.nb - C.nm >= kMergeAt<KMAX> || C.nb > kCap - W)) {
         if (C.nb > kCap) set_error(m, JZT_ERR_INTERNAL, kStageLeaf);  // cannot happen
         merge_distances<KMAX>(buf, C, lane, act);
-        if (__any_sync(kFull, C.nb > kCap - W)) compact<KMAX>(buf, C, k, lane);
+        if (__any_sync(kFull, C.nb > kCap - W)) {
+          if (__any_sync(kFull, C.nb > C.nm)) merge_distances<KMAX>(buf, C, lane, act);
+          compact<KMAX>(buf, C, k, lane);
+        }
       }
     }
   }
@@ -1087,7 +1099,8 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
         if (!stop && issued < nb) issue(issued);
       }
     }
-    // final k-th distance, drop the entries beyond it, exact (d2, index) selection
+    // final k-th distance (fewer than kMergeAt entries are unmerged here), drop the
+    // entries beyond it, exact (d2, index) selection
     merge_distances<KMAX>(S.buf, C, lane, act);
     compact<KMAX>(S.buf, C, k, lane);
     RegTopK<unsigned long long, KMAX> T;
