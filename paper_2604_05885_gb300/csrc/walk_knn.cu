@@ -926,8 +926,11 @@ __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt
 // One warp per query leaf.  Source leaves of the (sorted) interaction list are
 // staged into shared memory by bulk copies, kStages ahead of the computation;
 // the list metadata (source box and point range) is read 32 entries at a time,
-// one entry per lane.  Each query lane keeps its k best (d2, index) keys in a
-// sorted register list (RegTopK); its last key is the running k-th distance.
+// one entry per lane.  Each query lane keeps the k smallest distances seen so
+// far in a sorted register list of floats, whose last entry is the running k-th
+// distance; every source point at or below it is buffered as a (d2, index) pair
+// in the lane's shared-memory buffer, and the exact k best (d2, index) keys are
+// selected from that buffer once the list is done.
 //
 // k above 32 runs several passes (LB = true after the first): pass j fills the
 // row's columns col0 = 32 j .. col0 + k - 1 (row length k_row) with the k best
