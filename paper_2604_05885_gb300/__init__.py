@@ -402,6 +402,19 @@ def fof(xyz: torch.Tensor, b: float, periodic_L: float = 0.0, workspace=None, st
     return lab
 
 
+def assign_lanes(sizes, n_lanes: int) -> list[int]:
+    """Lane of every job: longest processing time first, each job to the lane
+    with the fewest points so far (the lowest lane on ties).  Host logic only."""
+    order = sorted(range(len(sizes)), key=lambda j: -sizes[j])
+    load = [0] * n_lanes
+    lane_of = [0] * len(sizes)
+    for j in order:
+        lane = min(range(n_lanes), key=lambda q: load[q])
+        lane_of[j] = lane
+        load[lane] += sizes[j]
+    return lane_of
+
+
 class Batch:
     """Independent kNN / FoF jobs run on concurrent lanes through jzt_batch_run,
     optionally captured once into a CUDA graph and replayed.
@@ -423,13 +436,7 @@ class Batch:
         n_lanes = max(1, min(int(n_lanes), nj))
         self.n_lanes = n_lanes
         sizes = [int(s["points"].shape[0]) for s in sets]
-        order = sorted(range(nj), key=lambda j: -sizes[j])
-        load = [0] * n_lanes
-        lane_of = [0] * nj
-        for j in order:
-            lane = min(range(n_lanes), key=lambda q: load[q])
-            lane_of[j] = lane
-            load[lane] += sizes[j]
+        lane_of = assign_lanes(sizes, n_lanes)
         need = [0] * n_lanes
         for j, st in enumerate(sets):
             _check_xyz(st["points"])

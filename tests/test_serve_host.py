@@ -51,3 +51,27 @@ def test_batched_specs_shape():
     assert 0.4 < ops.count("knn") / len(ops) < 0.6
     again = workloads.batched_specs(512, 4)
     assert specs == again  # seeded
+
+
+def test_lane_assignment_longest_first():
+    """Longest-processing-time order, each job to the least-loaded lane: every job
+    placed once, and the largest lane load within Graham's bound (4/3 - 1/(3m))
+    of the optimum, which brute force gives on small inputs."""
+    import itertools
+    pytest.importorskip("torch")
+    from paper_2604_05885_gb300 import assign_lanes
+    rng = np.random.default_rng(3)
+    for trial in range(60):
+        nj, m = int(rng.integers(1, 8)), int(rng.integers(1, 4))
+        sizes = [int(v) for v in rng.integers(1, 50, nj)]
+        lane_of = assign_lanes(sizes, m)
+        assert len(lane_of) == nj and all(0 <= q < m for q in lane_of)
+        load = [0] * m
+        for j, q in enumerate(lane_of):
+            load[q] += sizes[j]
+        opt = min(max(sum(sizes[j] for j in range(nj) if a[j] == q) for q in range(m))
+                  for a in itertools.product(range(m), repeat=nj))
+        assert max(load) <= (4 / 3 - 1 / (3 * m)) * opt + 1e-9
+    # equal jobs go round the lanes in job order; the largest job takes lane 0
+    assert assign_lanes([5] * 6, 3) == [0, 1, 2, 0, 1, 2]
+    assert assign_lanes([1, 9, 3], 2)[1] == 0
