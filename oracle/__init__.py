@@ -15,6 +15,8 @@ Contents, each following the paper (jz-tree, Stuecker et al.):
   - ``morton_keys``   -- 3 x 21-bit interleaved keys (Sec. II-A: integer Morton key;
     x is the most significant coordinate, as in the z-order comparator).
   - ``zsort``         -- stable sort by key.
+  - ``zorder_msb`` / ``zorder_less`` / ``zorder_sort`` -- the full-precision float
+    comparator of Sec. II-A (Eq. msb, EMAX = 128 for float32; -0 read as +0).
   - ``gap_levels``    -- lvl_i between sorted neighbours i-1, i (Sec. II-C, eq. lvl_i),
     with the sentinel gaps at 0 and N.
   - ``node_sizes``    -- n_i, the size of the smallest node holding i-1 and i
@@ -224,6 +226,53 @@ def zsort(keys):
     """Stable ascending sort by key: (sorted keys, perm) with perm[i] = original index."""
     perm = np.argsort(keys, kind="stable").astype(np.int64)
     return np.asarray(keys)[perm], perm
+
+
+# ---- full-precision z-order of float32 points (Sec. II-A, Eq. msb and the
+# comparator after it; the float alternative to the 21-bit integer keys) ----
+
+ZORDER_EMAX32 = 128  # one above the largest float32 exponent
+
+
+def _exact32(v) -> int:
+    """The float32 value v as the exact integer v * 2^149 (every float32, normal or
+    subnormal, is an integer multiple of 2^-149); -0 and +0 both give 0."""
+    bits = int(np.asarray(v, dtype=np.float32).view(np.uint32))
+    e, f = (bits >> 23) & 0xFF, bits & 0x7FFFFF
+    m = f if e == 0 else (f | 0x800000) << (e - 1)  # (2^23 + f) 2^(e-150) = (2^23 + f) 2^(e-1) 2^-149
+    return -m if bits >> 31 else m
+
+
+def zorder_msb(a, b) -> int:
+    """msb(a, b) of Eq. msb for float32 a, b: EMAX when the signs differ, otherwise
+    the power of two of the highest bit at which |a| and |b| differ when both are
+    written as fixed-point numbers (this is max(ex(a), ex(b)) when the exponents
+    differ and ex + msb_fixed of the mantissas when they agree).  Equal values give
+    -150, below every bit a float32 has.  Zero counts as positive."""
+    x, y = _exact32(a), _exact32(b)
+    if (x < 0) != (y < 0):
+        return ZORDER_EMAX32
+    return (abs(x) ^ abs(y)).bit_length() - 150
+
+
+def zorder_less(p, q) -> bool:
+    """p strictly before q in the z-order of Sec. II-A: k is the first dimension of
+    the largest msb(p_i, q_i), and p precedes q when p_k < q_k (equal vectors
+    precede neither way)."""
+    ms = [zorder_msb(p[i], q[i]) for i in range(len(p))]
+    k = ms.index(max(ms))
+    return _exact32(p[k]) < _exact32(q[k])
+
+
+def zorder_sort(xyz) -> np.ndarray:
+    """Stable sort of float32 points by the comparator of Sec. II-A at full
+    precision: perm with perm[i] = original index of the i-th point in z order."""
+    import functools
+    pts = np.asarray(xyz, dtype=np.float32)
+
+    def cmp(i, j):
+        return -1 if zorder_less(pts[i], pts[j]) else (1 if zorder_less(pts[j], pts[i]) else 0)
+    return np.array(sorted(range(len(pts)), key=functools.cmp_to_key(cmp)), dtype=np.int64)
 
 
 def _bit_length(v: np.ndarray) -> np.ndarray:

@@ -1,0 +1,87 @@
+"""Pins of the oracle's full-precision float z-order (Sec. II-A, Eq. msb and the
+comparator after it), each from something other than the oracle itself: the
+paper's msb_fixed example, the cases of Eq. msb, the integer Morton order it must
+reproduce on the 2^-21 grid, numeric order along one axis, the axioms of a strict
+weak order (brute force), and invariance under exact power-of-two scaling."""
+import os
+
+import numpy as np
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "msb_example.txt")
+
+
+def _binary(s: str) -> float:
+    whole, frac = s.split(".")
+    return int(whole, 2) + sum(int(c) * 2.0 ** -(i + 1) for i, c in enumerate(frac))
+
+
+def test_paper_msb_example():
+    rows = dict(line.split() for line in open(GOLDEN) if line.strip() and not line.startswith("#"))
+    a, b = _binary(rows["a"]), _binary(rows["b"])
+    assert (a, b) == (169.3125, 165.6875)
+    assert oracle.zorder_msb(a, b) == int(rows["msb"]) == oracle.zorder_msb(b, a)
+
+
+def test_msb_cases():
+    assert oracle.zorder_msb(-1.0, 1.0) == oracle.ZORDER_EMAX32 == 128      # signs differ
+    assert oracle.zorder_msb(-2.0 ** -149, 3.0e38) == 128
+    assert oracle.zorder_msb(1.0, 2.0) == 1                                 # exponents differ: the larger
+    assert oracle.zorder_msb(0.75, 3.0) == 1
+    assert oracle.zorder_msb(-0.75, -3.0) == 1
+    assert oracle.zorder_msb(2.0 ** 127 * 1.5, 1.0) == 127
+    assert oracle.zorder_msb(1.5, 1.25) == -1                               # same exponent: ex + msb_fixed
+    assert oracle.zorder_msb(12.0, 13.0) == 0
+    assert oracle.zorder_msb(2.0 ** -149, 2.0 ** -148) == -148              # subnormals
+    assert oracle.zorder_msb(0.0, 2.0 ** -149) == -149
+    assert oracle.zorder_msb(2.0 ** -126, 2.0 ** -126 - 2.0 ** -149) == -126  # normal vs subnormal
+    assert oracle.zorder_msb(5.0, 5.0) == -150 == oracle.zorder_msb(-0.0, 0.0)
+
+
+def test_grid_points_follow_the_integer_morton_order():
+    """On the 2^-21 grid of [0,1)^3 the comparator and the interleaved 21-bit key
+    (x the most significant coordinate) give the same order."""
+    rng = np.random.default_rng(11)
+    q = rng.integers(0, 1 << 21, (3000, 3))
+    q[100:140] = q[100]                                     # exact duplicates: stable order
+    q[200:260, 1:] = q[200, 1:]                             # points sharing two coordinates
+    x = (q.astype(np.float64) / (1 << 21)).astype(np.float32)
+    _, perm = oracle.zsort(oracle.interleave(q.astype(np.int64)))
+    assert np.array_equal(oracle.zorder_sort(x), perm)
+
+
+def test_one_axis_is_numeric_order():
+    rng = np.random.default_rng(12)
+    v = np.concatenate([rng.standard_normal(200) * 10.0 ** rng.uniform(-40, 38, 200),
+                        [0.0, -0.0, 2.0 ** -149, -2.0 ** -149, 3.0e38, -3.0e38, 1.0, 1.0]]).astype(np.float32)
+    x = np.zeros((len(v), 3), np.float32)
+    x[:, 0] = v
+    want = np.argsort(v.astype(np.float64) + 0.0, kind="stable")  # -0 == +0
+    assert np.array_equal(oracle.zorder_sort(x), want)
+    y = np.zeros((len(v), 3), np.float32)                       # along z alone, the same
+    y[:, 2] = v
+    assert np.array_equal(oracle.zorder_sort(y), want)
+
+
+def test_strict_weak_order_brute_force():
+    rng = np.random.default_rng(13)
+    pool = np.array([0.0, -0.0, 1.0, -1.0, 0.5, 3.0, -2.5, 2.0 ** -140, 7.0e20, -1.0e-30], np.float32)
+    x = rng.choice(pool, (36, 3)).astype(np.float32)
+    x[::5] = rng.standard_normal((8, 3)).astype(np.float32)
+    n = len(x)
+    less = np.array([[oracle.zorder_less(x[i], x[j]) for j in range(n)] for i in range(n)])
+    same = np.array([[bool(np.all(x[i] == x[j])) for j in range(n)] for i in range(n)])
+    assert not less.diagonal().any()                            # irreflexive
+    assert not (less & less.T).any()                            # asymmetric
+    assert np.array_equal(~(less | less.T), same)               # only equal vectors are unordered
+    two = (less.astype(np.int64) @ less.astype(np.int64)) > 0   # i < j < k for some j
+    assert not (two & ~less).any()                              # transitive
+
+
+def test_power_of_two_scaling_keeps_the_order():
+    rng = np.random.default_rng(14)
+    x = (rng.standard_normal((800, 3)) * 10.0 ** rng.uniform(-3, 3, (800, 3))).astype(np.float32)
+    base = oracle.zorder_sort(x)
+    for s in (-40, -3, 5, 60):
+        assert np.array_equal(oracle.zorder_sort((x * np.float32(2.0 ** s)).astype(np.float32)), base)
