@@ -2,7 +2,8 @@
 comparator after it), each from something other than the oracle itself: the
 paper's msb_fixed example, the cases of Eq. msb, the integer Morton order it must
 reproduce on the 2^-21 grid, numeric order along one axis, the axioms of a strict
-weak order (brute force), and invariance under exact power-of-two scaling."""
+weak order (brute force), invariance under exact power-of-two scaling, and the
+order of full-precision (278 bits per coordinate) interleaved integer keys."""
 import os
 
 import numpy as np
@@ -85,3 +86,35 @@ def test_power_of_two_scaling_keeps_the_order():
     base = oracle.zorder_sort(x)
     for s in (-40, -3, 5, 60):
         assert np.array_equal(oracle.zorder_sort((x * np.float32(2.0 ** s)).astype(np.float32)), base)
+
+
+def _wide_key(p) -> int:
+    """Morton key of a float32 point at full precision: each coordinate becomes the
+    278-bit unsigned U = 2^277 + m (v >= 0) or 2^277 - 1 - m (v < 0), where
+    m = |v| 2^149 is exact, and the three U are interleaved bit by bit, x most
+    significant.  Same-sign values keep the XOR of their magnitudes and the sign
+    becomes the top bit, so this integer order is the comparator's order."""
+    import struct
+    key = 0
+    us = []
+    for v in p:
+        bits = struct.unpack("<I", struct.pack("<f", float(v)))[0]
+        e, f = (bits >> 23) & 0xFF, bits & 0x7FFFFF
+        m = f if e == 0 else (f + (1 << 23)) << (e - 1)
+        neg = bool(bits >> 31) and m != 0
+        us.append((1 << 277) - 1 - m if neg else (1 << 277) + m)
+    for b in range(278):
+        for d in range(3):
+            key |= ((us[d] >> b) & 1) << (3 * b + 2 - d)
+    return key
+
+
+def test_comparator_equals_wide_integer_morton_order():
+    rng = np.random.default_rng(15)
+    x = (rng.standard_normal((500, 3)) * 10.0 ** rng.uniform(-44, 37, (500, 3))).astype(np.float32)
+    x[::9, 0] = 0.0
+    x[::13, 1] = -0.0
+    x[::17] = x[4]
+    keys = [_wide_key(p) for p in x]
+    want = sorted(range(len(x)), key=lambda i: (keys[i], i))
+    assert oracle.zorder_sort(x).tolist() == want
