@@ -59,3 +59,18 @@ def test_zeldovich_recipe():
     mean_p = [power[(kk >= s - 0.5) & (kk < s + 0.5)].mean() for s in shells]
     slope = np.polyfit(np.log(shells), np.log(mean_p), 1)[0]
     assert abs(slope + 4.0) < 0.4
+
+
+def test_clustered_device_recipe_on_the_host_generator():
+    """The device-side draw (torch's generator; run here on the CPU) keeps the
+    clustered recipe: grid, reproducibility by seed, 70 % of points in blobs."""
+    torch = pytest.importorskip("torch")
+    spatial = pytest.importorskip("scipy.spatial")
+    a = workloads.clustered_device(20000, 3, "cpu", n_blobs=10, sigma_lo=1e-4, sigma_hi=1e-4)
+    b = workloads.clustered_device(20000, 3, "cpu", n_blobs=10, sigma_lo=1e-4, sigma_hi=1e-4)
+    c = workloads.clustered_device(20000, 4, "cpu", n_blobs=10, sigma_lo=1e-4, sigma_hi=1e-4)
+    assert torch.equal(a, b) and not torch.equal(a, c)
+    x = a.numpy()
+    _on_grid(x)
+    near = spatial.cKDTree(x, boxsize=1.0).query_ball_point(x, 2e-3, return_length=True)
+    assert abs(np.mean(near > 50) - 0.7) < 0.01
