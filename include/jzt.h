@@ -41,7 +41,7 @@ extern "C" {
 typedef enum jzt_error {
     JZT_OK = 0,
     JZT_ERR_INVALID = -1,      /* bad argument (N, k, b, L, null pointer, alignment) */
-    JZT_ERR_UNSUPPORTED = -2,  /* valid but not implemented here (k > 32) */
+    JZT_ERR_UNSUPPORTED = -2,  /* valid but not implemented here (k > 256; FoF on a query tree) */
     JZT_ERR_CUDA = -3,         /* a CUDA runtime call failed (message in jzt_last_error) */
     JZT_ERR_WORKSPACE = -4,    /* ws_bytes below jzt_workspace_bytes() */
     JZT_ERR_CAPACITY = -5,     /* device: node or interaction-list capacity exceeded */
