@@ -53,6 +53,16 @@ class Request:
     _pts: object = field(default=None, repr=False)    # its points, while a build needs them
 
 
+def _check_requests(reqs):
+    """Workspaces are sized for k <= K_MAX: reject anything else before any work."""
+    for r in reqs:
+        if r.op == "knn":
+            if not 1 <= int(r.k) <= min(K_MAX, int(r.n)):
+                raise ValueError(f"request {r.rid}: k = {r.k} outside 1..min({K_MAX}, n)")
+        elif r.op != "fof":
+            raise ValueError(f"request {r.rid}: op must be 'knn' or 'fof'")
+
+
 def _out_bytes(r: Request) -> int:
     return r.n * r.k * 8 if r.op == "knn" else r.n * 4
 
@@ -180,6 +190,7 @@ class Server:
         arrival times (all requests queued at t = 0).  Returns the requests with
         t_done set (seconds since the start of the run)."""
         reqs = sorted(requests, key=lambda r: r.t_arrival)
+        _check_requests(reqs)
         torch.cuda.synchronize(self.dev)
         t0_ev = torch.cuda.Event(enable_timing=True)
         t0_ev.record(torch.cuda.current_stream(self.dev))
@@ -255,6 +266,7 @@ class PlainServer:
 
     def run(self, requests, realtime: bool = True, poll_sleep: float = 5e-5):
         reqs = sorted(requests, key=lambda r: r.t_arrival)
+        _check_requests(reqs)
         s = self.stream
         torch.cuda.synchronize(self.dev)
         t0_ev = torch.cuda.Event(enable_timing=True)

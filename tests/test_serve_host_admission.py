@@ -103,3 +103,14 @@ def test_busy_tree_is_not_evicted_and_requests_wait(fake_serve):
     # a set's tree serves one request at a time, so each set is built once and reused
     assert srv.stats["builds"] == 2 and srv.stats["hits"] == 6 and srv.stats["evictions"] == 0
     assert srv.stats["max_inflight"] == 2
+
+
+def test_invalid_requests_are_rejected_before_any_work(fake_serve):
+    serve, payload, built = fake_serve
+    srv = serve.Server(payload, n_lanes=2, hbm_budget=1e12, device="cpu")
+    R = serve.Request
+    for bad in (R(0, 0, 1000, "knn", 64), R(1, 1, 10, "knn", 16), R(2, 2, 1000, "knn", 0),
+                R(3, 3, 1000, "sort")):
+        with pytest.raises(ValueError):
+            srv.run([R(9, 9, 1000, "knn", 8), bad], realtime=False, poll_sleep=0.0)
+    assert built == []  # nothing was started
