@@ -118,3 +118,39 @@ def test_comparator_equals_wide_integer_morton_order():
     keys = [_wide_key(p) for p in x]
     want = sorted(range(len(x)), key=lambda i: (keys[i], i))
     assert oracle.zorder_sort(x).tolist() == want
+
+
+def _u278(v) -> int:
+    import struct
+    bits = struct.unpack("<I", struct.pack("<f", float(v)))[0]
+    e, f = (bits >> 23) & 0xFF, bits & 0x7FFFFF
+    m = f if e == 0 else (f + (1 << 23)) << (e - 1)
+    return (1 << 277) - 1 - m if (bits >> 31) and m else (1 << 277) + m
+
+
+def test_windowed_radix_plan_equals_comparator():
+    """The GPU plan for the float z-order: T = the highest bit at which any
+    coordinate of the set varies (bits above it are common to all points), then
+    63-bit keys from aligned 21-bit windows [T-20, T], [T-41, T-21], ... of the
+    three coordinates, and a stable sort by the windows from the lowest to the
+    highest (LSD) -- the same order as the comparator."""
+    rng = np.random.default_rng(16)
+    for scale_lo, scale_hi in ((-2, 2), (-44, 37), (-1, 0)):
+        x = (rng.standard_normal((400, 3)) * 10.0 ** rng.uniform(scale_lo, scale_hi, (400, 3))).astype(np.float32)
+        if scale_hi == 0:
+            x = np.abs(x) % 1.0                                   # box-bounded, non-negative
+        x[::23] = x[7]
+        u = [[_u278(v) for v in p] for p in x]
+        top = max((min(c) ^ max(c)).bit_length() for c in zip(*u)) - 1
+        perm = list(range(len(x)))
+        lows = list(range(top - 20, -21, -21))[::-1]              # window bottoms, lowest first
+        for lo in lows:
+            def key(i, lo=lo):
+                k = 0
+                for b in range(20, -1, -1):
+                    for d in range(3):
+                        bit = (u[i][d] >> (lo + b)) & 1 if lo + b >= 0 else 0
+                        k = (k << 1) | bit
+                return k
+            perm = sorted(perm, key=key)                          # stable: LSD over the windows
+        assert perm == oracle.zorder_sort(x).tolist()
