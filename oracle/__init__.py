@@ -15,8 +15,9 @@ Contents, each following the paper (jz-tree, Stuecker et al.):
   - ``morton_keys``   -- 3 x 21-bit interleaved keys (Sec. II-A: integer Morton key;
     x is the most significant coordinate, as in the z-order comparator).
   - ``zsort``         -- stable sort by key.
-  - ``zorder_msb`` / ``zorder_less`` / ``zorder_sort`` -- the full-precision float
-    comparator of Sec. II-A (Eq. msb, EMAX = 128 for float32; -0 read as +0).
+  - ``zorder_msb`` / ``zorder_less`` / ``zorder_sort`` / ``zorder_level`` -- the
+    full-precision float comparator of Sec. II-A (Eq. msb, EMAX = 128 for float32;
+    -0 read as +0) and the node level of Sec. II-C (Eq. lvl) on top of it.
   - ``gap_levels``    -- lvl_i between sorted neighbours i-1, i (Sec. II-C, eq. lvl_i),
     with the sentinel gaps at 0 and N.
   - ``node_sizes``    -- n_i, the size of the smallest node holding i-1 and i
@@ -262,6 +263,15 @@ def zorder_less(p, q) -> bool:
     ms = [zorder_msb(p[i], q[i]) for i in range(len(p))]
     k = ms.index(max(ms))
     return _exact32(p[k]) < _exact32(q[k])
+
+
+def zorder_level(p, q) -> int:
+    """lvl(p, q) = (msb(p_k, q_k) + 1) d - k of Sec. II-C (Eq. lvl) at full float32
+    precision, k the dimension the comparator compares (d = len(p)).  Equal
+    vectors give (-150 + 1) d, below every real level."""
+    ms = [zorder_msb(p[i], q[i]) for i in range(len(p))]
+    k = ms.index(max(ms))
+    return (ms[k] + 1) * len(p) - k
 
 
 def zorder_sort(xyz) -> np.ndarray:

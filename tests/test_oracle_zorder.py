@@ -154,3 +154,24 @@ def test_windowed_radix_plan_equals_comparator():
                 return k
             perm = sorted(perm, key=key)                          # stable: LSD over the windows
         assert perm == oracle.zorder_sort(x).tolist()
+
+
+def test_float_level_matches_integer_gap_level_on_the_grid():
+    """Eq. lvl at full precision against the integer form bit_length(key XOR key):
+    on the 2^-21 grid of [0,1)^3 bit j of a coordinate weighs 2^(j-21), so the two
+    differ by the constant 3 * 21 = 63."""
+    rng = np.random.default_rng(17)
+    q = rng.integers(0, 1 << 21, (2000, 3))
+    q[50:60] = q[50]
+    q[300:400, :2] = q[300, :2]
+    x = (q.astype(np.float64) / (1 << 21)).astype(np.float32)
+    skeys, perm = oracle.zsort(oracle.interleave(q.astype(np.int64)))
+    lvl = oracle.gap_levels(skeys)
+    for i in range(1, len(x)):
+        a, b = x[perm[i - 1]], x[perm[i]]
+        if skeys[i - 1] != skeys[i]:
+            assert oracle.zorder_level(a, b) == lvl[i] - 63
+        else:
+            assert oracle.zorder_level(a, b) == -447
+    assert oracle.zorder_level((1.0, 0.0, 0.0), (1.0, 0.5, 0.0)) == (-1 + 1) * 3 - 1
+    assert oracle.zorder_level((-1.0, 0.0, 0.0), (1.0, 0.0, 0.0)) == (128 + 1) * 3
