@@ -615,19 +615,6 @@ __device__ __forceinline__ float wrap1(float d, float L, float invL) {
   return d - L * rintf(d * invL);
 }
 
-template <bool PER>
-__device__ __forceinline__ float point_box_d2(float4 q, const NodeRec& b, float L) {
-  float s = 0.0f;
-  const float qq[3] = {q.x, q.y, q.z};
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const float g = PER ? gap_rd_per(qq[d], qq[d], b.lo[d], b.hi[d], L)
-                        : gap_rd(qq[d], qq[d], b.lo[d], b.hi[d]);
-    s = __fmaf_rd(g, g, s);
-  }
-  return s * kLowSlack;
-}
-
 #ifndef JZT_L2L_STAGES
 #define JZT_L2L_STAGES 2
 #endif
