@@ -17,7 +17,9 @@ Contents, each following the paper (jz-tree, Stuecker et al.):
   - ``zsort``         -- stable sort by key.
   - ``zorder_msb`` / ``zorder_less`` / ``zorder_sort`` / ``zorder_level`` -- the
     full-precision float comparator of Sec. II-A (Eq. msb, EMAX = 128 for float32;
-    -0 read as +0) and the node level of Sec. II-C (Eq. lvl) on top of it.
+    -0 read as +0) and the node level of Sec. II-C (Eq. lvl) on top of it;
+    ``zorder_gap_levels`` / ``zorder_node_sizes_brute`` -- lvl_i and n_i of Sec. II-C
+    on that order.
   - ``gap_levels``    -- lvl_i between sorted neighbours i-1, i (Sec. II-C, eq. lvl_i),
     with the sentinel gaps at 0 and N.
   - ``node_sizes``    -- n_i, the size of the smallest node holding i-1 and i
@@ -272,6 +274,49 @@ def zorder_level(p, q) -> int:
     ms = [zorder_msb(p[i], q[i]) for i in range(len(p))]
     k = ms.index(max(ms))
     return (ms[k] + 1) * len(p) - k
+
+
+ZORDER_INDEX_LEVEL = -479   # equal vectors: level bit_length((i-1) XOR i) - 479, in [-478, -447]
+ZORDER_SENTINEL_LEVEL = 388  # the gaps before the first and after the last point: above (128+1)*3
+
+
+def zorder_gap_levels(sxyz) -> np.ndarray:
+    """lvl_i for gaps i = 0..N between z-sorted float32 points i-1 and i (Sec. II-C)
+    at full precision (``zorder_level``).  As for the integer keys, equal points are
+    made distinct by their sorted position, whose levels lie below every level of
+    distinct points, and the two outer gaps carry a sentinel above every level."""
+    x = np.asarray(sxyz, dtype=np.float32)
+    n = len(x)
+    lvl = np.full(n + 1, ZORDER_SENTINEL_LEVEL, dtype=np.int64)
+    for i in range(1, n):
+        if np.all(x[i - 1] == x[i]):
+            lvl[i] = ((i - 1) ^ i).bit_length() + ZORDER_INDEX_LEVEL
+        else:
+            lvl[i] = zorder_level(x[i - 1], x[i])
+    return lvl
+
+
+def zorder_node_sizes_brute(sxyz, lvl=None) -> np.ndarray:
+    """n_i (Sec. II-C) on the float z-order by direct counting: the points that agree
+    with point i above level lvl_i (zorder_level at most lvl_i), or, for a gap
+    between equal points, the equal points in the same aligned block of sorted
+    positions.  O(N^2): tiny N only."""
+    x = np.asarray(sxyz, dtype=np.float32)
+    n = len(x)
+    if lvl is None:
+        lvl = zorder_gap_levels(x)
+    out = np.full(n + 1, n, dtype=np.int64)
+    for i in range(1, n):
+        g = int(lvl[i])
+        cnt = 0
+        for j in range(n):
+            if g > ZORDER_INDEX_LEVEL + 32:
+                cnt += zorder_level(x[j], x[i]) <= g
+            else:
+                bits = g - ZORDER_INDEX_LEVEL
+                cnt += bool(np.all(x[j] == x[i])) and (j >> bits) == (i >> bits)
+        out[i] = cnt
+    return out
 
 
 def zorder_sort(xyz) -> np.ndarray:

@@ -175,3 +175,41 @@ def test_float_level_matches_integer_gap_level_on_the_grid():
             assert oracle.zorder_level(a, b) == -447
     assert oracle.zorder_level((1.0, 0.0, 0.0), (1.0, 0.5, 0.0)) == (-1 + 1) * 3 - 1
     assert oracle.zorder_level((-1.0, 0.0, 0.0), (1.0, 0.0, 0.0)) == (128 + 1) * 3
+
+
+def test_float_tree_levels_and_sizes_match_the_integer_tree_on_the_grid():
+    rng = np.random.default_rng(18)
+    q = rng.integers(0, 1 << 21, (400, 3))
+    q[10:30] = q[10]                                            # a run of equal points
+    q[100:160, 0] = q[100, 0]
+    x = (q.astype(np.float64) / (1 << 21)).astype(np.float32)
+    skeys, perm = oracle.zsort(oracle.interleave(q.astype(np.int64)))
+    lvl_i, n_i = oracle.gap_levels(skeys), oracle.node_sizes(skeys)
+    sx = x[oracle.zorder_sort(x)]
+    lvl_f = oracle.zorder_gap_levels(sx)
+    inner = slice(1, len(x))
+    dup = np.concatenate([[False], skeys[1:] == skeys[:-1]])[inner]
+    d = lvl_f[inner] - lvl_i[inner]
+    assert np.all(d[~dup] == -63) and np.all(d[dup] == -447)
+    assert np.array_equal(oracle.zorder_node_sizes_brute(sx, lvl_f), n_i)
+
+
+def test_float_node_sizes_are_contiguous_segments():
+    """The points of a node form one segment of the z order, bounded by the first
+    gaps on either side whose level exceeds the node's (extreme ranges, duplicates)."""
+    rng = np.random.default_rng(19)
+    x = (rng.standard_normal((70, 3)) * 10.0 ** rng.uniform(-30, 30, (70, 3))).astype(np.float32)
+    x[5:12] = x[5]
+    x[40:44, 1:] = x[40, 1:]
+    sx = x[oracle.zorder_sort(x)]
+    lvl = oracle.zorder_gap_levels(sx)
+    sizes = oracle.zorder_node_sizes_brute(sx, lvl)
+    n = len(sx)
+    for i in range(1, n):
+        l = i - 1
+        while l > 0 and lvl[l] <= lvl[i]:
+            l -= 1
+        r = i
+        while r < n - 1 and lvl[r + 1] <= lvl[i]:
+            r += 1
+        assert sizes[i] == r - l + 1
