@@ -19,7 +19,7 @@ Contents, each following the paper (jz-tree, Stuecker et al.):
     full-precision float comparator of Sec. II-A (Eq. msb, EMAX = 128 for float32;
     -0 read as +0) and the node level of Sec. II-C (Eq. lvl) on top of it;
     ``zorder_gap_levels`` / ``zorder_node_sizes_brute`` -- lvl_i and n_i of Sec. II-C
-    on that order.
+    on that order, which ``plane_splits_from_sizes`` turns into tree-planes.
   - ``gap_levels``    -- lvl_i between sorted neighbours i-1, i (Sec. II-C, eq. lvl_i),
     with the sentinel gaps at 0 and N.
   - ``node_sizes``    -- n_i, the size of the smallest node holding i-1 and i
@@ -472,9 +472,17 @@ def plane_splits(skeys, nmax0: int = 48, c: int = 8, n_target: int = 1000, n_pla
     f_max > 0 adds the regularisation of Sec. II-D: after the count splits of a
     plane, every candidate gap whose level exceeds lvl_max^(p) is kept as well."""
     k = np.asarray(skeys, dtype=np.uint64)
-    n = k.shape[0]
-    nsz = node_sizes(k)
-    lvl = gap_levels(k)
+    return plane_splits_from_sizes(node_sizes(k), gap_levels(k), nmax0, c, n_target, n_planes, f_max)
+
+
+def plane_splits_from_sizes(nsz, lvl, nmax0: int = 48, c: int = 8, n_target: int = 1000, n_planes=None,
+                            f_max: float = 0.0):
+    """``plane_splits`` from the node sizes n_i and gap levels lvl_i of any z order
+    (the integer keys, or the float order of ``zorder_gap_levels``; the
+    regularisation's volume classes are defined on the integer levels only)."""
+    nsz = np.asarray(nsz, dtype=np.int64)
+    lvl = np.asarray(lvl, dtype=np.int64)
+    n = nsz.shape[0] - 1
     if n_planes is None:
         n_planes = num_planes(n, nmax0, c, n_target)
     gaps = []

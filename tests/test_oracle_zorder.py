@@ -213,3 +213,20 @@ def test_float_node_sizes_are_contiguous_segments():
         while r < n - 1 and lvl[r + 1] <= lvl[i]:
             r += 1
         assert sizes[i] == r - l + 1
+
+
+def test_float_tree_planes_match_the_integer_tree_on_the_grid():
+    rng = np.random.default_rng(20)
+    q = rng.integers(0, 1 << 21, (600, 3))
+    q[200:260] = q[200]
+    x = (q.astype(np.float64) / (1 << 21)).astype(np.float32)
+    skeys, _ = oracle.zsort(oracle.interleave(q.astype(np.int64)))
+    sx = x[oracle.zorder_sort(x)]
+    lvl = oracle.zorder_gap_levels(sx)
+    sizes = oracle.zorder_node_sizes_brute(sx, lvl)
+    for nmax0, c, nt in ((4, 2, 20), (8, 4, 10), (48, 8, 1000)):
+        spl_i, gaps_i = oracle.plane_splits(skeys, nmax0, c, nt)
+        spl_f, gaps_f = oracle.plane_splits_from_sizes(sizes, lvl, nmax0, c, nt)
+        assert len(spl_i) == len(spl_f)
+        assert all(np.array_equal(a, b) for a, b in zip(gaps_i, gaps_f))
+        assert all(np.array_equal(a, b) for a, b in zip(spl_i, spl_f))
