@@ -49,10 +49,14 @@ def parse():
     ap.add_argument("--k", type=int, default=16)
     ap.add_argument("--b-frac", type=float, default=0.2)
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--ref-queries", type=int, default=1 << 18,
+                    help="kNN rows per step of --impl reference (random points of the full set)")
     ap.add_argument("--ref-side", type=float, default=0.25,
-                    help="side of the sub-cube timed per step by --impl reference")
-    ap.add_argument("--cpu-side", type=float, default=0.75,
-                    help="side of the sub-cube of the workload timed on the CPU")
+                    help="side of the sub-cube whose FoF is timed per step by --impl reference")
+    ap.add_argument("--cpu-queries", type=int, default=1 << 20,
+                    help="kNN rows timed on the CPU for cpu_baseline")
+    ap.add_argument("--cpu-side", type=float, default=0.5,
+                    help="side of the sub-cube whose FoF is timed on the CPU for cpu_baseline")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--kdtree-side", type=float, default=0.5,
                     help="side of the sub-cube timed with scipy's k-d tree (context)")
@@ -139,24 +143,33 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def cpu_baseline(x, n_side, k, b, side, threads=0):
-    """The oracle (cell-list kNN + cell-list FoF, all host cores) on the points of
-    the sub-cube [0, side)^3 of the workload, treated as an open box."""
+def cpu_baseline(x, n_side, k, b, q_sample, fof_side, threads=0, seed=0):
+    """The oracle (float64 cell lists, all host cores) on a bounded sample of the
+    workload, scaled to a rate for the whole of it:
+
+    * kNN: the rows of ``q_sample`` points drawn at random from the full periodic
+      set (the same problem; every row costs about the same), time x N / q_sample;
+    * FoF: the points of the sub-cube [0, fof_side)^3 as an open box (FoF needs
+      the whole connected set, so a sub-volume stands in), time x N / its points.
+    """
     import numpy as np
     import oracle
-    sel = np.all(x < np.float32(side), axis=1)
+    n = x.shape[0]
+    q = np.sort(np.random.default_rng(seed).choice(n, min(int(q_sample), n), replace=False))
+    sel = np.all(x < np.float32(fof_side), axis=1)
     xs = np.ascontiguousarray(x[sel])
     cores = oracle.num_threads(threads)
     t0 = time.perf_counter()
-    oracle.knn_cells(xs, k, 0.0, threads=threads)
+    oracle.knn_cells(x, k, 1.0, queries=q, threads=threads)
     t1 = time.perf_counter()
     oracle.fof_cells(xs, b, 0.0, threads=threads)
     t2 = time.perf_counter()
-    n = xs.shape[0]
-    return {"value": n / (t2 - t0), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} points of the sub-cube [0,{side})^3 of the {n_side}^3 Zel'dovich set, "
-                      f"open box; cell-list kNN k={k} ({t1 - t0:.1f} s) + cell-list FoF ({t2 - t1:.1f} s)",
-            "seconds": t2 - t0}
+    est = (t1 - t0) * n / len(q) + (t2 - t1) * n / xs.shape[0]
+    return {"value": n / est, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"kNN k={k}: rows of {len(q)} random points of the full periodic {n_side}^3 Zel'dovich "
+                      f"set ({t1 - t0:.1f} s); FoF b={b:.3g}: the {xs.shape[0]} points of the sub-cube "
+                      f"[0,{fof_side})^3 as an open box ({t2 - t1:.1f} s); each part scaled to all {n} points",
+            "seconds": t2 - t0, "seconds_full_estimate": est}
 
 
 def batched_run(a, dev, log):
@@ -428,17 +441,20 @@ def main():
         import numpy as np  # noqa: F401
         vals = []
         for s in range(a.warmup + a.steps):
-            cb = cpu_baseline(x, n_side, k, b, a.ref_side)
+            cb = cpu_baseline(x, n_side, k, b, a.ref_queries, a.ref_side, seed=s)
             if s >= a.warmup:
                 vals.append(cb)
         v = sorted(c["value"] for c in vals)[len(vals) // 2]
         cb = dict(vals[-1])
         cb["value"] = v
+        cfg_ref = dict(cfg, step="oracle on a bounded sample per step, scaled to the whole workload",
+                       sample=cb["sample"], parallelism=f"host cores x{cb['cores']}")
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup,
                 "ms_per_step": 1000.0 * sum(c["seconds"] for c in vals) / len(vals),
+                "ms_per_step_full_workload_estimate": 1000.0 * sum(c["seconds_full_estimate"] for c in vals) / len(vals),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": cfg, "cpu_baseline": cb,
+                "data": "synthetic", "config": cfg_ref, "cpu_baseline": cb,
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -520,17 +536,48 @@ def main():
     jzt.profile_read()
 
     # FoF catalogue (Sec. IV-B): build + FoF + group order + reductions, groups >= 20; on the
-    # benchmark set (all singletons at b = 0.2 spacings) and on the 2^24 clustered periodic set
+    # benchmark set (all singletons at b = 0.2 spacings) and on the 2^24 clustered periodic set.
+    # The clustered set (4096 blobs, 7 M groups) also gets the plain rates: build + FoF and
+    # build + kNN (k = 32), since FoF on the benchmark set links nothing.
     cat = catalogue_timing(x_dev, L, b, params, ws, lab, stream, dev)
+    clu = {}
     try:
-        xc = torch.from_numpy(workloads.clustered(1 << 24, 2)).to(dev)
-        wsc = jzt.alloc_workspace(xc.shape[0], 0, params, dev)
-        labc = torch.empty(xc.shape[0], dtype=torch.int32, device=dev)
-        cat_c = catalogue_timing(xc, 1.0, 0.2 / 256, params, wsc, labc, stream, dev)
-        cat_c["workload"] = "clustered 2^24, periodic, seed 2, b = 0.2/256"
-        del xc, wsc, labc
+        wc, xc_h = workloads.config_clustered_16m()
+        xc = torch.from_numpy(xc_h).to(dev)
+        nc = xc.shape[0]
+        wsc = jzt.alloc_workspace(nc, wc.k, params, dev)
+        labc = torch.empty(nc, dtype=torch.int32, device=dev)
+        cat_c = catalogue_timing(xc, wc.periodic_L, wc.b, params, wsc, labc, stream, dev)
+        cat_c["workload"] = f"{wc.name}, seed 2, b = 0.2/256"
+        ic = torch.empty((nc, wc.k), dtype=torch.int32, device=dev)
+        dc = torch.empty((nc, wc.k), dtype=torch.float32, device=dev)
+        for name, op in (("fof", lambda t: t.fof(wc.b, out=labc)), ("knn", lambda t: t.knn(wc.k, out=(ic, dc)))):
+            def one():
+                t = jzt.build(xc, periodic_L=wc.periodic_L, workspace=wsc, params=params)
+                op(t)
+                return t
+            tc = one()
+            tc.status(raise_on_error=True)
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            for _ in range(3):
+                tc = one()
+            c1.record(stream)
+            torch.cuda.synchronize(dev)
+            tc.status(raise_on_error=True)
+            ms_c = c0.elapsed_time(c1) / 3
+            clu[name] = {"workload": wc.name, "n": nc, "periodic_L": wc.periodic_L,
+                         "k" if name == "knn" else "b": wc.k if name == "knn" else wc.b,
+                         "step": f"build + {'kNN' if name == 'knn' else 'FoF'}", "ms_per_step": ms_c,
+                         "value": nc / (ms_c / 1000.0), "unit": UNIT}
+            if name == "fof":
+                clu[name]["groups"] = int(torch.unique(labc).numel())
+            del tc
+        del xc, wsc, labc, ic, dc
     except Exception as exc:  # noqa: BLE001  (reported, not fatal for the main line)
-        cat_c = {"error": str(exc)[:200]}
+        cat_c = cat_c if "cat_c" in locals() else {"error": str(exc)[:200]}
+        clu["error"] = str(exc)[:200]
     jzt.profile_read()
 
     del ws, idx, d2, lab, tree
@@ -645,7 +692,8 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "clocks": clk, "e2e": e2e, "e2e_serial": e2e_serial, "gpu_launches": launches,
-            "fof_catalogue": cat, "fof_catalogue_clustered": cat_c, "knn_build_plus_walk": zo, "roofline": roofline,
+            "fof_catalogue": cat, "fof_catalogue_clustered": cat_c, "fof_clustered": clu.get("fof"),
+            "knn_clustered": clu.get("knn"), "knn_build_plus_walk": zo, "roofline": roofline,
             "roofline_sort": roof_sort, "roofline_build": roof_build,
             "phases_ms_per_step": {ph: phase_ms[ph] / steps for ph in phase_ms},
             "knn_particles_per_s": n / ((build_ms + knn_ms) / 1000.0) if knn_ms else None,
@@ -654,7 +702,7 @@ def main():
             "ilist_entries": st["ilist_entries"], "n_nodes": [v for v in st["n_nodes"] if v],
             "knn_plane_entries": [v for v in st["knn_plane_entries"] if v],
             "knn_l2l_entries_examined": st["knn_stats"][0], "knn_l2l_leaves_scanned": st["knn_stats"][1],
-            "knn_l2l_candidates_queued": st["knn_stats"][2], "knn_l2l_heap_insertions": st["knn_stats"][3],
+            "knn_l2l_candidates_queued": st["knn_stats"][2],
             "p50_p99_latency": None}
     del x_dev
     torch.cuda.synchronize(dev)
@@ -674,7 +722,7 @@ def main():
                                    "one_call_p99_ms": sv["one_call_per_request"]["p99_ms"],
                                    "arrival_rate_per_s": sv["arrival_rate_per_s"]}
     if rank == 0 and not a.no_cpu and world == 1:
-        line["cpu_baseline"] = cpu_baseline(x, n_side, k, b, a.cpu_side)
+        line["cpu_baseline"] = cpu_baseline(x, n_side, k, b, a.cpu_queries, a.cpu_side)
         line["cpu_kdtree"] = cpu_kdtree(x, n_side, k, a.kdtree_side)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -243,20 +243,29 @@ int jzt_batch_run(const jzt_job *jobs, int n_jobs, const jzt_params *p,
                   void *const *lane_streams, int n_lanes, void *stream, int32_t *d_job_status);
 
 /* Allocation-free form of jzt_knn (the paper has no counterpart: this is for
- * callers that may not allocate device memory, e.g. inside a framework that owns
- * all device allocations, or during stream capture).  Same results as jzt_knn
- * (rows in input order), but the scratch space is a fixed 16 MiB device array
- * inside the library rather than a caller workspace; the caller still owns
- * d_xyz, d_idx and d_dist2.  Limits: 1 <= N <= 65536, 1 <= k <= min(32, N);
- * larger sizes return JZT_ERR_INVALID with a message naming the limit.  Calls no
- * allocator.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
- * All calls share the one array per device: calls that overlap on the GPU (on
- * different streams or threads) race and must be serialised by the caller; each
- * call re-initialises what it needs, the rest keeps the previous call's data.
- * info: NULL to return after enqueueing the work; otherwise the call
- * synchronises `stream` and fills *info like jzt_status (device-side errors are
- * then returned as the call's result). */
+ * callers that may not allocate device memory, e.g. code inside a framework that
+ * owns all device allocations, or a real-time path that must not enter the
+ * allocator).  Same results as jzt_knn (rows in input order), but the scratch
+ * space is a fixed 16 MiB device array inside the library rather than a caller
+ * workspace; the caller still owns d_xyz, d_idx and d_dist2.  Limits:
+ * 1 <= N <= 65536, 1 <= k <= min(32, N); larger sizes return JZT_ERR_INVALID with
+ * a message naming the limit.  Calls no allocator.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current, so make that first call before any stream capture; the address is kept
+ * for the life of the process, so do not use this entry point after
+ * cudaDeviceReset.  All calls share the one array per device: calls that overlap
+ * on the GPU (on different streams or threads) race and must be serialised by
+ * the caller; each call re-initialises what it needs, the rest keeps the
+ * previous call's data.
+ * The interaction lists grow with the data, so even within the limits a
+ * clustered or duplicate-heavy set can run out of the fixed array: a device-side
+ * JZT_ERR_CAPACITY that no retry cures (the array cannot grow; use jzt_knn with
+ * a workspace of the size jzt_status reports).  After any device-side error
+ * every output entry is set to index -1, distance NaN.
+ * info: NULL to return after enqueueing the work (device-side errors are then
+ * visible only as those -1 / NaN rows); otherwise the call synchronises `stream`
+ * and fills *info like jzt_status (device-side errors are then returned as the
+ * call's result). */
 int jzt_knn_noalloc(const float *d_xyz, int64_t n, int k, float periodic_L,
                     int32_t *d_idx, float *d_dist2, void *stream, jzt_status_info *info);
 

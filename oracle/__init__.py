@@ -209,14 +209,41 @@ def quantise(xyz, periodic_L=0.0):
     return np.clip(q, 0, (1 << KEY_BITS) - 1).astype(np.uint64)
 
 
-def interleave(q) -> np.ndarray:
-    """Morton key: bit j of q_x -> key bit 3j+2, of q_y -> 3j+1, of q_z -> 3j."""
+def interleave_bits(q) -> np.ndarray:
+    """Morton key: bit j of q_x -> key bit 3j+2, of q_y -> 3j+1, of q_z -> 3j
+    (one bit at a time; the plain form of the definition)."""
     q = np.asarray(q, dtype=np.uint64)
     key = np.zeros(q.shape[0], dtype=np.uint64)
     for j in range(KEY_BITS):
         for d in range(3):
             bit = (q[:, d] >> np.uint64(j)) & np.uint64(1)
             key |= bit << np.uint64(3 * j + (2 - d))
+    return key
+
+
+def _spread_byte_table() -> np.ndarray:
+    """spread[v] for v < 256: bit j of v moved to bit 3j (the definition, per byte)."""
+    t = np.zeros(256, dtype=np.uint64)
+    for v in range(256):
+        w = 0
+        for j in range(8):
+            w |= ((v >> j) & 1) << (3 * j)
+        t[v] = w
+    return t
+
+
+_SPREAD = _spread_byte_table()
+
+
+def interleave(q) -> np.ndarray:
+    """The same key as ``interleave_bits``, one byte of each coordinate at a time:
+    byte b of q_d (bits 8b..8b+7) lands on key bits 3(8b+j) + (2-d)."""
+    q = np.asarray(q, dtype=np.uint64)
+    key = np.zeros(q.shape[0], dtype=np.uint64)
+    for d in range(3):
+        for b in range(3):  # 21 bits = bytes 0, 1, 2 (the top byte holds 5 bits)
+            byte = ((q[:, d] >> np.uint64(8 * b)) & np.uint64(0xFF)).astype(np.intp)
+            key |= _SPREAD[byte] << np.uint64(24 * b + (2 - d))
     return key
 
 
@@ -331,11 +358,12 @@ def zorder_sort(xyz) -> np.ndarray:
 
 
 def _bit_length(v: np.ndarray) -> np.ndarray:
+    """Bit length of unsigned 64-bit values (0 for 0).  Each 32-bit half is exact
+    in float64, whose frexp exponent is the half's bit length."""
     v = np.asarray(v, dtype=np.uint64)
-    out = np.zeros(v.shape, dtype=np.int64)
-    for s in range(64):
-        out = np.where((v >> np.uint64(s)) != 0, s + 1, out)
-    return out
+    hi = (v >> np.uint64(32)).astype(np.float64)
+    lo = (v & np.uint64(0xFFFFFFFF)).astype(np.float64)
+    return np.where(hi > 0, 32 + np.frexp(hi)[1], np.frexp(lo)[1]).astype(np.int64)
 
 
 def gap_levels(skeys):
@@ -506,7 +534,26 @@ def plane_splits_from_sizes(nsz, lvl, nmax0: int = 48, c: int = 8, n_target: int
 
 
 def plane_nodes(sxyz, gaps):
-    """Per plane: (count[n_nodes], lo[n_nodes,3], hi[n_nodes,3]) of the sorted points."""
+    """Per plane: (count[n_nodes], lo[n_nodes,3], hi[n_nodes,3]) of the sorted points:
+    node j holds sorted points gaps[j] .. gaps[j+1]-1 (never empty), its box is their
+    coordinate-wise min and max (numpy's segmented reduction over those ranges)."""
+    x = np.asarray(sxyz, dtype=np.float32)
+    out = []
+    for g in gaps:
+        g = np.asarray(g, dtype=np.int64)
+        cnt = np.diff(g)
+        if len(cnt):
+            assert (cnt > 0).all(), "empty node"
+            lo = np.minimum.reduceat(x, g[:-1], axis=0)
+            hi = np.maximum.reduceat(x, g[:-1], axis=0)
+        else:
+            lo = hi = np.zeros((0, 3), np.float32)
+        out.append((cnt.astype(np.int64), lo.astype(np.float32), hi.astype(np.float32)))
+    return out
+
+
+def plane_nodes_loop(sxyz, gaps):
+    """``plane_nodes`` with one slice per node (the plain form, for small sets)."""
     x = np.asarray(sxyz, dtype=np.float32)
     out = []
     for g in gaps:

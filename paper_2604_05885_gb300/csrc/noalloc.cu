@@ -2,21 +2,29 @@
 //
 // Some callers cannot allocate device memory at all: code that runs inside a
 // framework which owns every device allocation (and forbids cudaMalloc behind
-// its back), code called while a stream is being captured into a CUDA graph
-// (where a cudaMalloc would break the capture), or embedded and real-time users
-// that must not hit the allocator on their call path.  For them this file
-// provides jzt_knn_noalloc: the same build + kNN walk as jzt_knn, with its
-// scratch space taken from one fixed device array compiled into the library
-// instead of a caller-provided workspace.  The caller still owns the input and
-// output buffers.
+// its back), or real-time and embedded users that must not enter the allocator
+// on their call path.  For them this file provides jzt_knn_noalloc: the same
+// build + kNN walk as jzt_knn, with its scratch space taken from one fixed
+// device array compiled into the library instead of a caller-provided
+// workspace.  The caller still owns the input and output buffers.
 //
 // The array is g_noalloc_ws below (kNoAllocBytes, 16 MiB).  Every GPU that loads
 // the library holds it until the process exits.  In host code its name is only a
 // host-side stand-in for the device symbol, so its device address is looked up
 // with cudaGetSymbolAddress, once per device, with that device current, and that
-// address is what the kernels receive.
+// address is what the kernels receive.  The cached address belongs to the CUDA
+// context of that first call: after cudaDeviceReset the entry point must not be
+// used again in the same process.
+//
+// The interaction lists grow with the data (clustered or duplicate-heavy sets
+// need longer lists), so even within the size limits a call can run out of the
+// fixed array (JZT_ERR_CAPACITY on the device).  The array cannot grow, so no
+// retry cures that; such a call fills every output row with index -1 and
+// distance NaN, so that a caller who does not read the status cannot mistake
+// the rows for results.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -57,6 +65,17 @@ int scratch_address(void** out) {
   return JZT_OK;
 }
 
+// After a failed build or walk (any device-side status), every output entry
+// becomes (-1, NaN).
+__global__ void k_poison_rows(const Meta* m, int32_t* idx, float* d2, int64_t n_entries) {
+  if (*reinterpret_cast<const volatile int32_t*>(&m->status) == 0) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_entries;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    idx[i] = -1;
+    d2[i] = __int_as_float(0x7fc00000);
+  }
+}
+
 }  // namespace
 }  // namespace jzt
 
@@ -90,6 +109,10 @@ extern "C" int jzt_knn_noalloc(const float* d_xyz, int64_t n, int k, float perio
   // tables it uses; nothing else in the array needs to start at zero.
   launch_build(d_xyz, n, pl, L, static_cast<char*>(ws), s);
   launch_knn(L, static_cast<char*>(ws), pl, k, 0, d_idx, d_dist2, s);
+  const int64_t entries = n * (int64_t)k;
+  k_poison_rows<<<(unsigned)std::min<int64_t>((entries + 255) / 256, 152 * 8), 256, 0, s>>>(
+      at<Meta>(static_cast<char*>(ws), L.meta), d_idx, d_dist2, entries);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_msg(JZT_ERR_CUDA, std::string("jzt_knn_noalloc launch: ") + cudaGetErrorString(e));
   if (info) return jzt_status(ws, stream, info);

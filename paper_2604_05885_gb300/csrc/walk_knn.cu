@@ -183,6 +183,17 @@ __device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, long
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return mbar_wait_n(bar, parity, kSpinLimit);
 }
+// Failure path: wait for a bulk copy this warp issued to land before the warp
+// leaves (a CTA must not exit while a copy still writes its shared memory).  The
+// copy reads at most 512 bytes of valid device memory, so it completes unless
+// the memory system itself has failed; the wait backs off with nanosleep and
+// still gives up after about a second rather than hang.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    if (mbar_try_wait(bar, parity)) return;
+    __nanosleep(1000);
+  }
+}
 
 constexpr int kN2NWarps = 4;
 constexpr int kMetaCap = 256;  // list entries whose metadata a warp caches in shared memory
@@ -1044,12 +1055,13 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
           if (!landed) {
             if (lane == 0) set_error(m, JZT_ERR_TIMEOUT, kStageLeaf);
             broken = true;
-            // give the copies still in flight a bounded chance to land before leaving
-            for (uint32_t r = done + 1; r < issued; ++r) {
+            // every copy this warp issued and has not consumed -- the one that
+            // timed out included -- must land before the warp leaves
+            for (uint32_t r = done; r < issued; ++r) {
               const int s2 = r % kStages;
-              if ((__float_as_int(S.meta[r][2].w) & 0xff) > 0)
-                (void)__all_sync(kFull, mbar_wait(&S.bar[s2], (parity >> s2) & 1u));
+              if ((__float_as_int(S.meta[r][2].w) & 0xff) > 0) mbar_drain(&S.bar[s2], (parity >> s2) & 1u);
             }
+            __syncwarp();
             break;
           }
           parity ^= 1u << st;

@@ -1,6 +1,10 @@
 """Helpers for the GPU parity tests."""
+import os
+
 import numpy as np
 import torch
+
+import workloads
 
 import oracle
 from tests import parity
@@ -46,3 +50,18 @@ def fof_parity(tree, x, b, L):
     s, lo = oracle.fof_bracket(x, b, L, cells=x.shape[0] > 6000)
     parity.check_fof(lab, s, lo)
     return lab
+
+
+CACHE = os.path.join(os.environ.get("TMPDIR", "/tmp"), "jzt_bench_cache")
+
+
+def zeldovich_cached(n_side=512):
+    """The n_side^3 Zel'dovich set (seed 3), cached as .npy between runs on one machine."""
+    path = os.path.join(CACHE, f"zeldovich_{n_side}_seed3.npy")
+    if os.path.exists(path):
+        return np.load(path)
+    x = workloads.zeldovich(n_side, 3)
+    os.makedirs(CACHE, exist_ok=True)
+    np.save(path + ".tmp.npy", x)
+    os.replace(path + ".tmp.npy", path)
+    return x

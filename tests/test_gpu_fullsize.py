@@ -9,30 +9,19 @@
 
 The oracle side runs on the host cores (float64), the GPU side through the C ABI.
 """
-import os
-
 import numpy as np
 import pytest
 
 import oracle
 import workloads
 from tests import parity
-from tests.gpu_util import to_dev
+from tests.gpu_util import to_dev, zeldovich_cached
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
-CACHE = os.path.join(os.environ.get("TMPDIR", "/tmp"), "jzt_bench_cache")
-
 
 def _zeldovich512():
-    path = os.path.join(CACHE, "zeldovich_512_seed3.npy")
-    if os.path.exists(path):
-        return np.load(path)
-    x = workloads.zeldovich(512, 3)
-    os.makedirs(CACHE, exist_ok=True)
-    np.save(path + ".tmp.npy", x)
-    os.replace(path + ".tmp.npy", path)
-    return x
+    return zeldovich_cached(512)
 
 
 def _run(x, k, b, L):

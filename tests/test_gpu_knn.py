@@ -75,9 +75,16 @@ def test_duplicates_and_degenerate_geometry():
     x = workloads.uniform(2000, 12)
     x[50:450] = x[50]            # 400 copies of one point
     x[600:700, 2] = x[600, 2]     # a flat patch
+    dup = np.arange(50, 450)
     for L in (0.0, 1.0):
         tree = jzt.build(to_dev(x), periodic_L=L, params=dict(nmax0=8, n_target=8))
-        idx, _ = knn_parity(tree, x, 16, L)
+        idx, d2 = knn_parity(tree, x, 16, L)
+        # duplicates tie exactly at d2 = 0: each copy lists the 16 lowest indices of
+        # the run, in index order (the parity rule alone would accept any order)
+        ri, _ = oracle.knn_brute(x, 16, L, queries=dup)
+        assert np.array_equal(idx[dup], ri)
+        assert np.array_equal(idx[dup], np.broadcast_to(np.arange(50, 66), (len(dup), 16)))
+        assert np.all(d2[dup] == 0.0)
     line = np.zeros((500, 3), np.float32)
     line[:, 1] = workloads.uniform(500, 13)[:, 1]
     tree = jzt.build(to_dev(line), periodic_L=0.0)

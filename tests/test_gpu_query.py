@@ -44,7 +44,18 @@ def test_query_on_source_points_and_duplicates():
     qry = np.concatenate([src[::7], np.repeat(src[3:4], 64, axis=0)])
     idx, d2 = jzt.knn_query(to_dev(src), to_dev(qry), 12, 1.0)
     _check(src, qry, 12, 1.0, idx, d2)
-    assert np.all(d2.cpu().numpy()[:, 0] == 0.0)
+    d2 = d2.cpu().numpy()
+    idx = idx.cpu().numpy()
+    assert np.all(d2[:, 0] == 0.0)
+    # a query on a duplicated source ties exactly at d2 = 0 with both copies: the
+    # lower index comes first; every row's exact zero-distance ties are in index order
+    ri, _ = oracle.knn_brute_sets(src, qry, 12, 1.0)
+    zero = d2 == 0.0
+    assert np.array_equal(np.where(zero, idx, -1), np.where(zero, ri, -1))
+    on_dup = np.nonzero((np.arange(len(qry)) * 7 < 500) & (np.arange(len(qry)) < len(src[::7])))[0]
+    assert len(on_dup) > 50
+    assert np.array_equal(idx[on_dup, :2], np.stack([on_dup * 7, on_dup * 7 + 3000], axis=1))
+    assert np.array_equal(idx[-64:], np.broadcast_to(ri[-1], (64, 12)))
 
 
 def test_query_far_from_sources_open_box():

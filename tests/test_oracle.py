@@ -75,6 +75,34 @@ def test_interleave_bits():
     assert int(k[5]) == (0b110) | (0b011 << 3) | (0b101 << 6)
 
 
+def test_interleave_forms_agree():
+    """The byte-table interleave equals the bit-by-bit definition (and the hand
+    values above hold for both)."""
+    rng = np.random.default_rng(5)
+    q = rng.integers(0, 1 << 21, (20000, 3)).astype(np.uint64)
+    q[:3] = [[0, 0, 0], [(1 << 21) - 1] * 3, [1 << 20, 1, 1 << 7]]
+    assert np.array_equal(oracle.interleave(q), oracle.interleave_bits(q))
+
+
+def test_bit_length_matches_python():
+    rng = np.random.default_rng(6)
+    v = np.concatenate([rng.integers(0, 2**63, 5000, dtype=np.uint64) >> rng.integers(0, 64, 5000).astype(np.uint64),
+                        np.array([0, 1, 2, 3, 2**32 - 1, 2**32, 2**53 + 1, 2**63, 2**64 - 1], dtype=np.uint64)])
+    assert oracle._bit_length(v).tolist() == [int(x).bit_length() for x in v]
+
+
+def test_plane_nodes_forms_agree():
+    """Segmented min/max boxes equal one slice per node."""
+    x = workloads.clustered(5000, 21, n_blobs=5)
+    sk, perm = oracle.zsort(oracle.morton_keys(x, 1.0))
+    _, gaps = oracle.plane_splits(sk, nmax0=8, c=4, n_target=10)
+    a = oracle.plane_nodes(x[perm], gaps)
+    b = oracle.plane_nodes_loop(x[perm], gaps)
+    assert len(a) == len(b) >= 3
+    for (ca, la, ha), (cb, lb, hb) in zip(a, b):
+        assert np.array_equal(ca, cb) and np.array_equal(la, lb) and np.array_equal(ha, hb)
+
+
 def _msb_int(a, b):
     x = a ^ b
     return x.bit_length() - 1 if x else -1
