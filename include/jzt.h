@@ -22,7 +22,7 @@
  *     detected synchronously.  Errors that depend on the data (capacity
  *     overflow, invalid coordinates, exhausted waits) are recorded in a
  *     status word inside the workspace and read with jzt_status().
- *   - Sizes: 1 <= N < 2^30 points.  xyz is N x 3 row-major float32 (x,y,z per
+ *   - Sizes: 1 <= N < 2^31 points.  xyz is N x 3 row-major float32 (x,y,z per
  *     point), 4-byte aligned (16-byte aligned takes the vector-load path).
  *   - periodic_L > 0 selects a periodic box [0,L)^3 with minimum-image
  *     distances (Sec. III-G); every coordinate must lie in [0,L).
@@ -63,7 +63,12 @@ typedef struct jzt_params {
     float reg_fmax;           /* f_max of the plane regularisation (Sec. II-D): 0 = off (default);
                                  > 0: every plane also splits wherever a gap's level exceeds
                                  lvl_max^(p), 2^lvl_max <= f_max V_90% -- results do not change */
-    int32_t reserved[6];      /* must be zero */
+    int32_t float_order;      /* 0 (default): 3 x 21-bit integer Morton keys of the quantised points;
+                                 1: the full-precision float z-order of Sec. II-A (Eq. msb and its
+                                 comparator; Eq. lvl at float32 precision), for data whose scales
+                                 span many orders of magnitude -- results do not change, only the
+                                 tree; needs 16 more workspace bytes per point; not with reg_fmax */
+    int32_t reserved[5];      /* must be zero */
 } jzt_params;
 
 typedef struct jzt_tree jzt_tree;  /* opaque; lives on the host, points into the workspace */
@@ -188,7 +193,8 @@ int jzt_fof(const float *d_xyz, int64_t n, float b, float periodic_L,
 int jzt_status(const void *d_ws, void *stream, jzt_status_info *info);
 
 /* Device pointers into the tree (valid while the tree lives):
- *   keys  -- N uint64 Morton keys, sorted ascending
+ *   keys  -- N uint64 Morton keys, sorted ascending (NULL for a tree built with
+ *            float_order = 1, which sorts by the float comparator and has no keys)
  *   pts   -- N float4 sorted points (x, y, z, and in .w the original index of
  *            the point as int32 bits)
  * and the number of planes.  Host-only, no CUDA call. */
@@ -214,7 +220,7 @@ enum { JZT_OP_KNN = 0, JZT_OP_FOF = 1 };
 
 typedef struct jzt_job {
     const float *d_xyz;   /* N x 3 float32 points (device) */
-    int64_t n;            /* 1 <= N < 2^30 */
+    int64_t n;            /* 1 <= N < 2^31 */
     float periodic_L;     /* > 0: periodic box [0,L)^3 */
     int32_t op;           /* JZT_OP_KNN or JZT_OP_FOF */
     int32_t k;            /* kNN: neighbours per point, 1..min(256, N) */

@@ -346,6 +346,37 @@ def zorder_node_sizes_brute(sxyz, lvl=None) -> np.ndarray:
     return out
 
 
+def zorder_node_sizes(sxyz, lvl=None) -> np.ndarray:
+    """n_i on the float z-order, counted outward from the gap: a node is a
+    contiguous range of the sorted points (it holds every point whose prefix
+    above its level agrees), so the count walks left from i-1 and right from i
+    while the points stay in the node.  Same values as ``zorder_node_sizes_brute``
+    (pinned against it), in O(sum of n_i)."""
+    x = np.asarray(sxyz, dtype=np.float32)
+    n = len(x)
+    if lvl is None:
+        lvl = zorder_gap_levels(x)
+    out = np.full(n + 1, n, dtype=np.int64)
+    for i in range(1, n):
+        g = int(lvl[i])
+        if g > ZORDER_INDEX_LEVEL + 32:
+            def inside(j):
+                return zorder_level(x[j], x[i]) <= g
+        else:
+            bits = g - ZORDER_INDEX_LEVEL
+
+            def inside(j):
+                return bool(np.all(x[j] == x[i])) and (j >> bits) == (i >> bits)
+        lo = i - 1
+        while lo - 1 >= 0 and inside(lo - 1):
+            lo -= 1
+        hi = i + 1
+        while hi < n and inside(hi):
+            hi += 1
+        out[i] = hi - lo
+    return out
+
+
 def zorder_sort(xyz) -> np.ndarray:
     """Stable sort of float32 points by the comparator of Sec. II-A at full
     precision: perm with perm[i] = original index of the i-th point in z order."""

@@ -58,7 +58,8 @@ class Params(ctypes.Structure):
     _fields_ = [("nmax0", ctypes.c_int32), ("plane_factor", ctypes.c_int32),
                 ("n_target", ctypes.c_int32), ("ngr", ctypes.c_int32),
                 ("alloc_fac_nodes", ctypes.c_float), ("alloc_fac_ilist", ctypes.c_float),
-                ("heap_size", ctypes.c_int32), ("reg_fmax", ctypes.c_float), ("reserved", ctypes.c_int32 * 6)]
+                ("heap_size", ctypes.c_int32), ("reg_fmax", ctypes.c_float), ("float_order", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class Job(ctypes.Structure):
@@ -279,13 +280,17 @@ class Tree:
         return labels, order, groups
 
     def arrays(self):
-        """(sorted keys uint64 view as int64 [N], sorted points float32 [N,4], n_planes)."""
+        """(sorted keys uint64 view as int64 [N] -- None for the float z-order, which
+        has no keys --, sorted points float32 [N,4], n_planes)."""
         kp, pp, npl = ctypes.c_void_p(0), ctypes.c_void_p(0), ctypes.c_int32(0)
         _check(lib.jzt_tree_arrays(self._h, ctypes.byref(kp), ctypes.byref(pp), ctypes.byref(npl)))
         ws = self.workspace
         base = ws.data_ptr()
-        koff, poff = kp.value - base, pp.value - base
-        keys = ws[koff:koff + 8 * self.n].view(torch.int64)
+        poff = pp.value - base
+        keys = None
+        if kp.value:
+            koff = kp.value - base
+            keys = ws[koff:koff + 8 * self.n].view(torch.int64)
         pts = ws[poff:poff + 16 * self.n].view(torch.float32).view(self.n, 4)
         return keys, pts, int(npl.value)
 

@@ -35,8 +35,9 @@ int resolve_params(const jzt_params* p, Params* out, const char** why) {
   P.fac_nodes = 2.0f;
   P.fac_ilist = 128.0f;
   P.reg_fmax = 0.0f;
+  P.float_order = 0;
   if (p) {
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
       if (p->reserved[i] != 0) {
         *why = "jzt_params.reserved must be zero";
         return JZT_ERR_INVALID;
@@ -49,6 +50,15 @@ int resolve_params(const jzt_params* p, Params* out, const char** why) {
     if (p->alloc_fac_nodes != 0.0f) P.fac_nodes = p->alloc_fac_nodes;
     if (p->alloc_fac_ilist != 0.0f) P.fac_ilist = p->alloc_fac_ilist;
     P.reg_fmax = p->reg_fmax;
+    P.float_order = p->float_order;
+  }
+  if (P.float_order != 0 && P.float_order != 1) {
+    *why = "float_order must be 0 or 1";
+    return JZT_ERR_INVALID;
+  }
+  if (P.float_order && P.reg_fmax > 0.0f) {
+    *why = "the regularisation (reg_fmax > 0) works on the integer keys only, not with float_order";
+    return JZT_ERR_UNSUPPORTED;
   }
   if (!(P.reg_fmax >= 0.0f) || std::isinf(P.reg_fmax)) {
     *why = "reg_fmax must be >= 0 and finite";
@@ -92,6 +102,7 @@ int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* L
   L.ngr = P.ngr;
   L.heap = P.heap;
   L.reg_fmax = P.reg_fmax;
+  L.float_order = P.float_order;
   L.n_planes = num_planes(n, P);
   // Node capacity per plane: fac * N / (N_max^(p)/2) (Eq. alloc_nodes).  The
   // estimate is not a bound (Sec. II-C), so the small upper planes get 4x the
@@ -123,6 +134,7 @@ int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* L
   L.vals_b = take(4 * (size_t)n);
   L.lookback = take((size_t)L.n_tiles_sort * kRadixBins * kRadixPasses * 4);
   L.pts = take(16 * (size_t)n);
+  if (L.float_order) L.pts_tmp = take(16 * (size_t)n);
   const int64_t scan_tiles = std::max<int64_t>((n + 1 + kScanTile - 1) / kScanTile, 1) + 1;
   L.scan_flags = take(8 * (size_t)scan_tiles);
   for (int p = 0; p <= L.n_planes; ++p) L.spl[p] = take(4 * (size_t)(L.cap_nodes[p] + 1));
@@ -174,8 +186,8 @@ struct jzt_tree {
 };
 
 static int check_n(int64_t n) {
-  if (n < 1 || n >= (int64_t(1) << 30))
-    return fail(JZT_ERR_INVALID, "N must satisfy 1 <= N < 2^30 (got " + std::to_string(n) + ")");
+  if (n < 1 || n >= (int64_t(1) << 31))
+    return fail(JZT_ERR_INVALID, "N must satisfy 1 <= N < 2^31 (got " + std::to_string(n) + ")");
   return JZT_OK;
 }
 
@@ -433,7 +445,7 @@ int jzt_status(const void* d_ws, void* stream, jzt_status_info* info) {
 int jzt_tree_arrays(const jzt_tree* t, const uint64_t** d_keys, const float** d_pts,
                     int32_t* n_planes) {
   if (!t) return fail(JZT_ERR_INVALID, "tree is null");
-  if (d_keys) *d_keys = at<uint64_t>(t->ws, t->L.keys_a);
+  if (d_keys) *d_keys = t->L.float_order ? nullptr : at<uint64_t>(t->ws, t->L.keys_a);
   if (d_pts) *d_pts = at<float>(t->ws, t->L.pts);
   if (n_planes) *n_planes = t->L.n_planes;
   return JZT_OK;

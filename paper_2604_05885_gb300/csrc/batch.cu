@@ -43,7 +43,7 @@ extern "C" int jzt_batch_run(const jzt_job* jobs, int n_jobs, const jzt_params* 
     const std::string tag = "job " + std::to_string(j) + ": ";
     if (!J.d_xyz) return fail_msg(JZT_ERR_INVALID, tag + "null points");
     if (reinterpret_cast<uintptr_t>(J.d_xyz) & 3u) return fail_msg(JZT_ERR_INVALID, tag + "points not 4-byte aligned");
-    if (J.n < 1 || J.n >= (int64_t(1) << 30)) return fail_msg(JZT_ERR_INVALID, tag + "N out of range");
+    if (J.n < 1 || J.n >= (int64_t(1) << 31)) return fail_msg(JZT_ERR_INVALID, tag + "N out of range");
     if (!std::isfinite(J.periodic_L)) return fail_msg(JZT_ERR_INVALID, tag + "periodic_L must be finite");
     if (J.lane < 0 || J.lane >= n_lanes) return fail_msg(JZT_ERR_INVALID, tag + "lane out of range");
     if (!d_lane_ws[J.lane] || (reinterpret_cast<uintptr_t>(d_lane_ws[J.lane]) & 255u))

@@ -11,14 +11,12 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "zorder.cuh"
 
 namespace jzt {
 
 namespace {
 
-constexpr uint32_t kFlagA = 1u << 30;  // look-back: tile aggregate published
-constexpr uint32_t kFlagP = 2u << 30;  // look-back: inclusive prefix published
-constexpr uint32_t kValMask = (1u << 30) - 1;
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -138,7 +136,7 @@ __global__ void k_init_meta(Meta* m, int n_planes) {
   }
   if (t < 32) m->tile_ctr[t] = 0;
   uint32_t* h = &m->radix_hist[0][0];
-  for (int i = t; i < kRadixPasses * kRadixBins; i += blockDim.x) h[i] = 0;
+  for (int i = t; i < kMaxRadixPasses * kMaxRadixBins; i += blockDim.x) h[i] = 0;
 }
 
 __global__ void k_zero_u64(unsigned long long* p, int64_t n) {
@@ -262,8 +260,8 @@ __device__ __forceinline__ uint64_t morton(float x, float y, float z, const floa
 __device__ __forceinline__ void hist_key(uint32_t (*sh)[kRadixBins], uint64_t key, bool valid) {
   const unsigned act = __ballot_sync(0xffffffffu, valid);
   if (!valid) return;
-#pragma unroll
   const int leader = __ffs(act) - 1;
+#pragma unroll
   for (int p = 0; p < kRadixPasses; ++p) {
     uint32_t d = (uint32_t)(key >> (p * kRadixBits)) & (kRadixBins - 1);
     const uint32_t d0 = __shfl_sync(act, d, leader);
@@ -329,16 +327,16 @@ __global__ void __launch_bounds__(256) k_keygen(const float* __restrict__ xyz, i
   __syncthreads();
   for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) {
     uint32_t v = (&sh[0][0])[i];
-    if (v) atomicAdd(&m->radix_hist[0][0] + i, v);
+    if (v) atomicAdd(&m->radix_hist[i / kRadixBins][i % kRadixBins], v);
   }
 }
 
-// Exclusive digit offsets per pass (one warp per pass).
-__global__ void k_radix_offsets(Meta* m) {
+// Exclusive digit offsets of `passes` passes of `bins` digits (one warp per pass).
+__global__ void k_radix_offsets(Meta* m, int passes, int bins) {
   const int p = warp_id();
-  if (p >= kRadixPasses) return;
+  if (p >= passes) return;
   uint32_t run = 0;
-  for (int b0 = 0; b0 < kRadixBins; b0 += 32) {
+  for (int b0 = 0; b0 < bins; b0 += 32) {
     uint32_t v = m->radix_hist[p][b0 + lane_id()];
     uint32_t inc = warp_incl_scan(v);
     m->radix_offsets[p][b0 + lane_id()] = run + inc - v;
@@ -348,34 +346,97 @@ __global__ void k_radix_offsets(Meta* m) {
 
 // ------------------------------------------------------------------ onesweep pass
 //
-// One stable counting pass of the LSD radix sort on digit `pass` (8 bits).
-// Tiles of 4096 keys are claimed in order through an atomic counter, so a tile
-// only ever waits (decoupled look-back) on tiles already running.  Keys are
-// ranked stably per warp with match.any, staged in shared memory in digit
-// order, and written out in runs that are contiguous in global memory.
+// One stable counting pass of the LSD radix sort on the BITS-bit digit at bit
+// `shift`.  Tiles of kSortTile keys are claimed in order through an atomic
+// counter, so a tile only ever waits (decoupled look-back) on tiles that are
+// already running.  A tile
+//  1. loads kSortIpt keys per thread (striped over the warp: coalesced);
+//  2. ranks every key among the keys of its warp with the same digit: the lanes
+//     holding that digit are found with one ballot per digit bit, and the
+//     lowest of them advances the warp's counter for the digit in shared memory;
+//  3. per digit: prefix over the warps, tile count, tile start (block scan); the
+//     tile counts are published for the later tiles at once;
+//  4. moves its keys into shared memory in digit order -- which needs nothing
+//     from other tiles -- and only then looks back for its global offsets, so
+//     the tiles before it have had that much longer to publish;
+//  5. writes its runs of equal digits, each contiguous in global memory.
+// GATHER (the last pass of the build) writes, instead of the permutation, the
+// sorted points float4(x, y, z, original index) read from the input by index.
+//
+// Look-back words (32 bit): 0 = nothing yet; kLbAgg | count = this tile's own
+// count; otherwise 1 + the inclusive prefix over tiles 0..t (at most 2^31).
+template <int BITS>
 struct SortSmem {
-  uint32_t whist[kSortThreads / 32][kRadixBins];
-  uint32_t tile_start[kRadixBins];
-  uint32_t gbase[kRadixBins];
+  static constexpr int kBins = 1 << BITS;
+  uint16_t whist[kSortThreads / 32][kBins];  // per-warp digit counts, then prefixes over warps
+  uint32_t tile_start[kBins];
+  uint32_t gbase[kBins];
   uint32_t tile;
   uint64_t stage_k[kSortTile];
   uint32_t stage_v[kSortTile];
 };
 
+constexpr uint32_t kLbAgg = 0xC0000000u;
 constexpr int kLookWin = 8;  // predecessor words read per look-back step
 
-__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const uint64_t* __restrict__ kin,
-                                                           const uint32_t* __restrict__ vin,
-                                                           uint64_t* __restrict__ kout,
-                                                           uint32_t* __restrict__ vout, int64_t n,
-                                                           int pass, uint32_t* lookback, Meta* m) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
+// Exclusive prefix of digit d over the tiles before `tile`: walk back over the
+// predecessors' words kLookWin at a time (independent relaxed loads: each word
+// carries its own flag and value), adding tile counts until an inclusive prefix
+// is found.  A word not yet published is polled again (bounded, with a short
+// sleep); on exhaustion the status becomes JZT_ERR_TIMEOUT.
+__device__ __forceinline__ uint32_t lookback_excl(const uint32_t* lookback, int64_t tile, int d, int bins,
+                                                  Meta* m) {
+  uint32_t excl = 0;
+  int64_t j = tile - 1;
+  long long spins = 0;
+  while (j >= 0) {
+    uint32_t v[kLookWin];
+#pragma unroll
+    for (int i = 0; i < kLookWin; ++i)
+      v[i] = j - i >= 0 ? ld_relaxed_u32(lookback + (size_t)(j - i) * bins + d) : 1u;  // 1u: prefix 0
+    int used = 0;
+    bool found = false, blocked = false;
+#pragma unroll
+    for (int i = 0; i < kLookWin; ++i) {
+      if (found || blocked) continue;
+      if (v[i] == 0u) {
+        blocked = true;
+      } else if ((v[i] & kLbAgg) == kLbAgg) {
+        excl += v[i] & ~kLbAgg;
+        ++used;
+      } else {
+        excl += v[i] - 1u;
+        found = true;
+      }
+    }
+    if (found) break;
+    j -= used;
+    if (blocked) {
+      if (++spins > kSpinLimit) {
+        set_error(m, JZT_ERR_TIMEOUT, kStageSort);
+        break;
+      }
+      if (failed(m)) break;
+      __nanosleep(32);
+    }
+  }
+  return excl;
+}
+
+template <int BITS, bool GATHER>
+__global__ void __launch_bounds__(kSortThreads, 3)
+    k_onesweep(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+               uint32_t* __restrict__ vout, int64_t n, int pass, int shift, uint32_t* lookback, Meta* m,
+               const float* __restrict__ xa, const float* __restrict__ xb, int64_t na, float4* __restrict__ pts) {
+  constexpr int kBins = 1 << BITS;
+  constexpr int DPT = kBins / kSortThreads;  // digits per thread
   constexpr int W = kSortThreads / 32;
+  static_assert(DPT >= 1 && DPT * kSortThreads == kBins, "whole digits per thread");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SortSmem<BITS>& S = *reinterpret_cast<SortSmem<BITS>*>(smem_raw);
   const int w = warp_id(), lane = lane_id(), t = threadIdx.x;
-  const int shift = pass * kRadixBits;
   if (t == 0) S.tile = atomicAdd(&m->tile_ctr[pass], 1u);
-  for (int i = t; i < W * kRadixBins; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+  for (int i = t; i < W * kBins; i += kSortThreads) (&S.whist[0][0])[i] = 0;
   __syncthreads();
   const int64_t tile = S.tile;
   const int64_t base = tile * kSortTile;
@@ -387,125 +448,99 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const uint64_t* __
   const int64_t wbase = base + (int64_t)w * (32 * kSortIpt);
 #pragma unroll
   for (int i = 0; i < kSortIpt; ++i) {
-    int64_t idx = wbase + i * 32 + lane;
-    bool ok = idx < n;
-    key[i] = ok ? kin[idx] : ~0ull;
+    const int64_t idx = wbase + i * 32 + lane;
+    const bool ok = idx < n;
+    key[i] = ok ? kin[idx] : 0ull;
     val[i] = ok ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
   }
+  const unsigned lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < kSortIpt; ++i) {
-    int64_t idx = wbase + i * 32 + lane;
-    uint32_t d = idx < n ? (uint32_t)(key[i] >> shift) & (kRadixBins - 1) : (uint32_t)kRadixBins;
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    int leader = __ffs(peers) - 1;
+    const bool valid = wbase + i * 32 + lane < n;
+    const uint32_t d = (uint32_t)(key[i] >> shift) & (kBins - 1);
+    unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+      const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+      peers &= ((d >> b) & 1u) ? bb : ~bb;
+    }
+    const int leader = valid ? __ffs(peers) - 1 : lane;
     uint32_t old = 0;
-    if (lane == leader && d < kRadixBins) {
+    if (valid && lane == leader) {
       old = S.whist[w][d];
-      S.whist[w][d] = old + __popc(peers);
+      S.whist[w][d] = (uint16_t)(old + __popc(peers));
     }
     old = __shfl_sync(0xffffffffu, old, leader);
-    rank[i] = old + __popc(peers & lanemask_lt());
+    rank[i] = old + __popc(peers & lt);
     __syncwarp();
   }
   __syncthreads();
-  // per digit: warp-exclusive prefixes and the tile count
-  uint32_t count;
-  {
-    const int d = t;  // kSortThreads == kRadixBins
+  // per digit (thread t owns digits t*DPT .. t*DPT+DPT-1): prefixes over warps and
+  // the tile count, then the tile start of each digit (block scan)
+  uint32_t cnt[DPT];
+  uint32_t tsum = 0;
+#pragma unroll
+  for (int e = 0; e < DPT; ++e) {
+    const int d = t * DPT + e;
     uint32_t run = 0;
 #pragma unroll
     for (int ww = 0; ww < W; ++ww) {
-      uint32_t v = S.whist[ww][d];
-      S.whist[ww][d] = run;
+      const uint32_t v = S.whist[ww][d];
+      S.whist[ww][d] = (uint16_t)run;
       run += v;
     }
-    count = run;
+    cnt[e] = run;
+    tsum += run;
   }
   uint32_t total;
-  uint32_t start = block_excl_scan<kSortThreads>(count, &total);
-  S.tile_start[t] = start;
-  // decoupled look-back, one digit per thread.  Each published word carries
-  // its own flag and count and nothing else is published through it, so the
-  // stores and loads are relaxed (no fences)
-  {
-    const int d = t;
-    uint32_t* lb = lookback + (size_t)tile * kRadixBins;
-    if (tile == 0) {
-      st_relaxed_u32(&lb[d], kFlagP | count);
-      S.gbase[d] = m->radix_offsets[pass][d];
-    } else {
-      st_relaxed_u32(&lb[d], kFlagA | count);
-      // walk back over the predecessors' (flag | count) words, kLookWin at a
-      // time (independent loads): add aggregates (A) until an inclusive prefix
-      // (P) is found; stop at an unpublished word and reload from there
-      uint32_t excl = 0;
-      int64_t j = tile - 1;
-      long long spins = 0;
-      bool found = false;
-      while (!found && j >= 0) {
-        uint32_t v[kLookWin];
+  uint32_t start = block_excl_scan<kSortThreads>(tsum, &total);
+  uint32_t* lb = lookback + (size_t)tile * kBins;
 #pragma unroll
-        for (int i = 0; i < kLookWin; ++i)
-          v[i] = j - i >= 0 ? ld_relaxed_u32(lookback + (size_t)(j - i) * kRadixBins + d) : kFlagP;
-        int used = 0;
-        bool blocked = false;
-#pragma unroll
-        for (int i = 0; i < kLookWin; ++i) {
-          if (found || blocked) continue;
-          const uint32_t f = v[i] & ~kValMask;
-          if (f == 0) {
-            blocked = true;
-            continue;
-          }
-          excl += v[i] & kValMask;
-          ++used;
-          if (f == kFlagP) found = true;
-        }
-        j -= used;
-        if (blocked && ++spins > kSpinLimit) {
-          set_error(m, JZT_ERR_TIMEOUT, kStageSort);
-          break;
-        }
-        if (blocked && failed(m)) break;
-      }
-      st_relaxed_u32(&lb[d], kFlagP | (excl + count));
-      S.gbase[d] = m->radix_offsets[pass][d] + excl;
-    }
+  for (int e = 0; e < DPT; ++e) {
+    const int d = t * DPT + e;
+    S.tile_start[d] = start;
+    start += cnt[e];
+    // tile 0 publishes its inclusive prefix (its count) directly
+    st_relaxed_u32(&lb[d], tile == 0 ? cnt[e] + 1u : (kLbAgg | cnt[e]));
   }
   __syncthreads();
-  // scatter into shared memory in digit order
+  // keys into shared memory in digit order
 #pragma unroll
   for (int i = 0; i < kSortIpt; ++i) {
-    int64_t idx = wbase + i * 32 + lane;
-    if (idx < n) {
-      uint32_t d = (uint32_t)(key[i] >> shift) & (kRadixBins - 1);
-      uint32_t pos = S.tile_start[d] + S.whist[w][d] + rank[i];
+    if (wbase + i * 32 + lane < n) {
+      const uint32_t d = (uint32_t)(key[i] >> shift) & (kBins - 1);
+      const uint32_t pos = S.tile_start[d] + S.whist[w][d] + rank[i];
       S.stage_k[pos] = key[i];
       S.stage_v[pos] = val[i];
     }
   }
+  // global offset of every digit of this tile: look back over the tiles before it
+#pragma unroll
+  for (int e = 0; e < DPT; ++e) {
+    const int d = t * DPT + e;
+    uint32_t excl = 0;
+    if (tile > 0) {
+      excl = lookback_excl(lookback, tile, d, kBins, m);
+      st_relaxed_u32(&lb[d], excl + cnt[e] + 1u);
+    }
+    S.gbase[d] = m->radix_offsets[pass][d] + excl;
+  }
   __syncthreads();
   for (int j = t; j < tile_n; j += kSortThreads) {
-    uint64_t k = S.stage_k[j];
-    uint32_t d = (uint32_t)(k >> shift) & (kRadixBins - 1);
-    uint32_t g = S.gbase[d] + (uint32_t)j - S.tile_start[d];
+    const uint64_t k = S.stage_k[j];
+    const uint32_t d = (uint32_t)(k >> shift) & (kBins - 1);
+    const uint32_t g = S.gbase[d] + (uint32_t)j - S.tile_start[d];
     if (g < (uint64_t)n) {  // always true unless a look-back wait gave up
       kout[g] = k;
-      vout[g] = S.stage_v[j];
+      const uint32_t v = S.stage_v[j];
+      if (GATHER) {
+        const uint32_t p = v < (uint64_t)n ? v : 0u;
+        const float* src = (int64_t)p < na ? xa + 3 * (int64_t)p : xb + 3 * ((int64_t)p - na);
+        pts[g] = make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), __uint_as_float(p));
+      } else {
+        vout[g] = v;
+      }
     }
-  }
-}
-
-// ------------------------------------------------------------------ gather
-// Combined index p < n1 reads xyz[p], otherwise xyz2[p - n1] (two point sets).
-__global__ void k_gather(const float* __restrict__ xyz, const float* __restrict__ xyz2, int64_t n1,
-                         const uint32_t* __restrict__ perm, int64_t n, float4* __restrict__ pts) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t p = perm[i];
-    if (p >= (uint64_t)n) p = 0;  // only after a failed sort (status already set)
-    const float* s = (int64_t)p < n1 ? xyz + 3 * (int64_t)p : xyz2 + 3 * ((int64_t)p - n1);
-    pts[i] = make_float4(__ldg(s), __ldg(s + 1), __ldg(s + 2), __uint_as_float(p));
   }
 }
 
@@ -637,13 +672,35 @@ __device__ __forceinline__ int level_ext(uint64_t ka, uint64_t kb, int64_t a, in
 constexpr int kSplitThreads = 256;
 constexpr int kSplitPer = kScanTile / kSplitThreads;  // gaps per thread
 
-__global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const uint64_t* __restrict__ keys,
+// The two sources of levels: integer Morton keys (levels -32..64 fit in int8)
+// and the float z-order of the sorted points themselves (levels -479..388).
+struct KeyLevels {
+  using Elem = uint64_t;
+  using Lvl = int8_t;
+  static constexpr int kNone = 127;
+  __device__ static Elem load(const void* src, int64_t pos) { return static_cast<const uint64_t*>(src)[pos]; }
+  __device__ static Elem pad() { return 0ull; }
+  __device__ static int level(const Elem& a, const Elem& b, int64_t ia, int64_t ib) { return level_ext(a, b, ia, ib); }
+};
+struct FloatLevels {
+  using Elem = float4;
+  using Lvl = int16_t;
+  static constexpr int kNone = kZNoLevel;
+  __device__ static Elem load(const void* src, int64_t pos) { return static_cast<const float4*>(src)[pos]; }
+  __device__ static Elem pad() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ static int level(const Elem& a, const Elem& b, int64_t ia, int64_t ib) { return zlevel(a, b, ia, ib); }
+};
+
+template <class Src>
+__global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const void* __restrict__ src,
                                                                int64_t n, int M, int32_t* spl0,
                                                                int64_t cap, unsigned long long* st,
                                                                Meta* m) {
-  __shared__ uint64_t s_key[kScanTile + 2 * 32 + 1];
-  __shared__ int8_t s_w[kScanTile + 32];
-  __shared__ int8_t s_pre[kScanTile + 32], s_suf[kScanTile + 32];
+  using Elem = typename Src::Elem;
+  using Lvl = typename Src::Lvl;
+  __shared__ Elem s_key[kScanTile + 2 * 32 + 1];
+  __shared__ Lvl s_w[kScanTile + 32];
+  __shared__ Lvl s_pre[kScanTile + 32], s_suf[kScanTile + 32];
   __shared__ uint32_t s_tile;
   const int reg_lvl = m->reg_lvl[0];
   if (threadIdx.x == 0) s_tile = atomicAdd(&m->tile_ctr[kCtrLeafSplits], 1u);
@@ -655,15 +712,15 @@ __global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const uint64_t* _
   const int nk = kScanTile + 2 * M;
   for (int t = threadIdx.x; t < nk; t += kSplitThreads) {
     int64_t pos = k0 + t;
-    s_key[t] = (pos >= 0 && pos < n) ? keys[pos] : 0ull;
+    s_key[t] = (pos >= 0 && pos < n) ? Src::load(src, pos) : Src::pad();
   }
   __syncthreads();
   // window levels w_j = level(j, j+M) for j in [g0 - M, g0 + T)
   for (int t = threadIdx.x; t < kScanTile + M; t += kSplitThreads) {
     int64_t j = k0 + t;
-    int v = 127;
-    if (j >= 0 && j + M < n) v = level_ext(s_key[t], s_key[t + M], j, j + M);
-    s_w[t] = (int8_t)v;
+    int v = Src::kNone;
+    if (j >= 0 && j + M < n) v = Src::level(s_key[t], s_key[t + M], j, j + M);
+    s_w[t] = (Lvl)v;
   }
   __syncthreads();
   // sliding minimum of width M over s_w: per block of M slots (aligned at 0),
@@ -671,15 +728,15 @@ __global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const uint64_t* _
   const int nw = kScanTile + M;
   for (int b0 = threadIdx.x * M; b0 < nw; b0 += kSplitThreads * M) {
     const int b1 = min(b0 + M, nw);
-    int8_t run = 127;
+    int run = Src::kNone;
     for (int t = b0; t < b1; ++t) {
-      run = min(run, s_w[t]);
-      s_pre[t] = run;
+      run = min(run, (int)s_w[t]);
+      s_pre[t] = (Lvl)run;
     }
-    run = 127;
+    run = Src::kNone;
     for (int t = b1 - 1; t >= b0; --t) {
-      run = min(run, s_w[t]);
-      s_suf[t] = run;
+      run = min(run, (int)s_w[t]);
+      s_suf[t] = (Lvl)run;
     }
   }
   __syncthreads();
@@ -693,10 +750,10 @@ __global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const uint64_t* _
       f = true;
     } else if (i < n) {
       int li = (int)(i - k0);  // s_key index of point i
-      int g = level_ext(s_key[li - 1], s_key[li], i - 1, i);
-      f = g > reg_lvl;  // regularisation (Sec. II-D); reg_lvl = 127 when off
+      int g = Src::level(s_key[li - 1], s_key[li], i - 1, i);
+      f = reg_lvl != kNoRegLevel && g > reg_lvl;  // regularisation (Sec. II-D)
       // windows j in [i - M, i - 1] (slots u .. u + M - 1, u = i - g0; slots of
-      // invalid j hold 127): split when the smallest window level is <= g
+      // invalid j hold kNone): split when the smallest window level is <= g
       const int u = (int)(i - g0);
       const int wmin = min((int)s_suf[u], (int)s_pre[u + M - 1]);
       f = f || wmin <= g;
@@ -786,6 +843,155 @@ __global__ void k_split_sizes(const uint64_t* __restrict__ keys, int64_t n,
         int64_t lb = first_ge_left(keys, i - 1, blk, kb);        // equal keys: keys[j] >= kb
         int64_t rb = first_gt_right(keys, i + 1, blk_end, kb);   // keys[j] > kb
         sz = rb - lb;
+      }
+    }
+    nsz[s] = (int32_t)sz;
+  }
+}
+
+// ---------------------------------------------------------------- float z-order (Sec. II-A)
+// The full-precision alternative to the 21-bit keys: the points are sorted by the
+// comparator of Eq. msb (zorder.cuh) with their original indices as the last key
+// (a stable sort of the input), by a merge sort -- bitonic tiles of kFSortTile
+// points in shared memory, then merge passes that split their output by merge
+// path -- and the tree's levels come from the sorted points themselves.
+constexpr int kFSortThreads = 256;
+constexpr int kFSortTile = 2048;
+constexpr int kFMergePer = 8;  // outputs per thread of a merge pass
+
+// Pads (index >= n) sort after every point.
+__device__ __forceinline__ bool fs_less(const float4& a, const float4& b, uint32_t n) {
+  const uint32_t ia = __float_as_uint(a.w), ib = __float_as_uint(b.w);
+  const bool pa = ia >= n, pb = ib >= n;
+  if (pa != pb) return pb;
+  if (pa) return ia < ib;
+  return zless(a, b);
+}
+
+// Tile t of the combined index (p < na: xa[p], else xb[p - na]) sorted into out.
+__global__ void __launch_bounds__(kFSortThreads) k_fsort_tiles(const float* __restrict__ xa,
+                                                               const float* __restrict__ xb, int64_t na,
+                                                               int64_t n, float4* __restrict__ out) {
+  __shared__ float4 s[kFSortTile];
+  const int64_t base = (int64_t)blockIdx.x * kFSortTile;
+  for (int i = threadIdx.x; i < kFSortTile; i += kFSortThreads) {
+    const int64_t p = base + i;
+    if (p < n) {
+      const float* src = p < na ? xa + 3 * p : xb + 3 * (p - na);
+      s[i] = make_float4(src[0], src[1], src[2], __uint_as_float((uint32_t)p));
+    } else {
+      s[i] = make_float4(0.f, 0.f, 0.f, __uint_as_float((uint32_t)min64(p, 0xffffffffll)));
+    }
+  }
+  __syncthreads();
+  const uint32_t nn = (uint32_t)n;
+  for (int size = 2; size <= kFSortTile; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int q = threadIdx.x; q < kFSortTile / 2; q += kFSortThreads) {
+        const int i = 2 * q - (q & (stride - 1));
+        const int j = i + stride;
+        const bool up = (i & size) == 0;
+        const float4 a = s[i], b = s[j];
+        if (up ? fs_less(b, a, nn) : fs_less(a, b, nn)) {
+          s[i] = b;
+          s[j] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < kFSortTile; i += kFSortThreads)
+    if (base + i < n) out[base + i] = s[i];
+}
+
+// One merge pass: runs [2wk, 2wk + w) and [2wk + w, 2wk + 2w) of in are merged
+// into out.  Each thread writes kFMergePer consecutive outputs; the number of
+// them taken from the first run is found by binary search on the merge path.
+__global__ void __launch_bounds__(256) k_fsort_merge(const float4* __restrict__ in, float4* __restrict__ out,
+                                                     int64_t n, int64_t w) {
+  const int64_t o0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kFMergePer;
+  if (o0 >= n) return;
+  const uint32_t nn = (uint32_t)n;
+  const int64_t base = (o0 / (2 * w)) * (2 * w);
+  const int64_t la = min64(w, n - base);
+  const int64_t lb = max64(0, min64(w, n - base - w));
+  const float4* A = in + base;
+  const float4* B = in + base + la;
+  const int64_t d = o0 - base;
+  int64_t lo = max64(0, d - lb), hi = min64(d, la);
+  while (lo < hi) {  // a = how many of the first d outputs come from A
+    const int64_t mid = (lo + hi) >> 1;
+    if (fs_less(B[d - 1 - mid], A[mid], nn)) hi = mid;
+    else lo = mid + 1;
+  }
+  int64_t ia = lo, ib = d - lo;
+  const int64_t end = min64(o0 + kFMergePer, base + la + lb);
+  for (int64_t o = o0; o < end; ++o) {
+    const bool take_a = ia < la && (ib >= lb || !fs_less(B[ib], A[ia], nn));
+    out[o] = take_a ? A[ia++] : B[ib++];
+  }
+}
+
+// Predicate-driven forms of the galloping searches of k_split_sizes.
+// Smallest j in [lo_lim, hi] such that in(j'') holds for all j'' in [j, hi], given in(hi).
+template <class Pred>
+__device__ __forceinline__ int64_t gallop_left(int64_t hi, int64_t lo_lim, Pred in) {
+  int64_t good = hi, step = 1;
+  while (good - step >= lo_lim && in(good - step)) {
+    good -= step;
+    step <<= 1;
+  }
+  int64_t bad = max64(lo_lim - 1, good - step);
+  while (good - bad > 1) {
+    const int64_t mid = bad + (good - bad) / 2;
+    if (in(mid)) good = mid; else bad = mid;
+  }
+  return good;
+}
+// Smallest j in [lo, hi_lim] with j == hi_lim or !in(j), given in(lo - 1).
+template <class Pred>
+__device__ __forceinline__ int64_t gallop_right(int64_t lo, int64_t hi_lim, Pred in) {
+  int64_t good = lo - 1, step = 1;
+  while (good + step < hi_lim && in(good + step)) {
+    good += step;
+    step <<= 1;
+  }
+  int64_t bad = min64(hi_lim, good + step);
+  while (bad - good > 1) {
+    const int64_t mid = good + (bad - good) / 2;
+    if (in(mid)) good = mid; else bad = mid;
+  }
+  return bad;
+}
+
+// n_i at every plane-0 split gap on the float order: the node at level lvl_i that
+// holds points i-1 and i is the contiguous range of the points j with
+// level(j, i) <= lvl_i (equal points: the equal points in the same aligned
+// block of sorted positions).
+__global__ void k_split_sizes_f(const float4* __restrict__ pts, int64_t n, const int32_t* __restrict__ spl0,
+                                int32_t* __restrict__ nsz, const Meta* m) {
+  if (failed(m)) return;
+  const int64_t ns = (int64_t)m->n_nodes[0] + 1;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = spl0[s];
+    int64_t sz = n;
+    if (i > 0 && i < n) {
+      const float4 pi = pts[i];
+      const int g = zlevel(pts[i - 1], pi, i - 1, i);
+      if (g > kZIndexLevel + 32) {
+        auto in = [&](int64_t j) { return zlevel(pts[j], pi, j, i) <= g; };
+        sz = gallop_right(i + 1, n, in) - gallop_left(i - 1, 0, in);
+      } else {
+        const int bits = g - kZIndexLevel;
+        const int64_t blk = (i >> bits) << bits;
+        const int64_t blk_end = min64(n, blk + (1ll << bits));
+        auto same = [&](int64_t j) {
+          int mk;
+          const float4 q = pts[j];
+          (void)zdim(q.x, q.y, q.z, pi.x, pi.y, pi.z, &mk);
+          return mk < 0;
+        };
+        sz = gallop_right(i + 1, blk_end, same) - gallop_left(i - 1, blk, same);
       }
     }
     nsz[s] = (int32_t)sz;
@@ -1042,14 +1248,37 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
   if (n_b > 0) bbox_part(d_b, n_b, periodic_L, m, s);
   k_finish_box<<<1, 32, 0, s>>>(m, periodic_L); note_launch();
   prof_end(kPhBox, s);
-  prof_begin(kPhKeys, s);
   uint64_t* keys_a = at<uint64_t>(ws, L.keys_a);
+  float4* pts = at<float4>(ws, L.pts);
+  if (L.float_order) {
+    // float z-order (Sec. II-A): merge sort of the points by the comparator; the
+    // passes alternate between pts and pts_tmp and end in pts
+    prof_begin(kPhSort, s);
+    float4* tmp = at<float4>(ws, L.pts_tmp);
+    int merge_passes = 0;
+    for (int64_t w = kFSortTile; w < n; w *= 2) ++merge_passes;
+    float4* cur = (merge_passes % 2) ? tmp : pts;
+    k_fsort_tiles<<<(unsigned)((n + kFSortTile - 1) / kFSortTile), kFSortThreads, 0, s>>>(d_a, d_b, n_a, n, cur);
+    note_launch();
+    for (int64_t w = kFSortTile; w < n; w *= 2) {
+      float4* nxt = (cur == pts) ? tmp : pts;
+      const int64_t threads = (n + kFMergePer - 1) / kFMergePer;
+      k_fsort_merge<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(cur, nxt, n, w);
+      note_launch();
+      cur = nxt;
+    }
+    prof_end(kPhSort, s);
+  } else {
+  prof_begin(kPhKeys, s);
   uint64_t* keys_b = at<uint64_t>(ws, L.keys_b);
   uint32_t* vals_a = at<uint32_t>(ws, L.vals_a);
   uint32_t* vals_b = at<uint32_t>(ws, L.vals_b);
-  keygen_part(d_a, n_a, m, keys_a, s);
-  if (n_b > 0) keygen_part(d_b, n_b, m, keys_a + n_a, s);
-  k_radix_offsets<<<1, 32 * kRadixPasses, 0, s>>>(m); note_launch();
+  // the passes alternate between the two key buffers and must end in keys_a:
+  // with an odd number of passes the keys start in keys_b
+  uint64_t* keys_in = (kRadixPasses % 2) ? keys_b : keys_a;
+  keygen_part(d_a, n_a, m, keys_in, s);
+  if (n_b > 0) keygen_part(d_b, n_b, m, keys_in + n_a, s);
+  k_radix_offsets<<<1, 32 * kRadixPasses, 0, s>>>(m, kRadixPasses, kRadixBins); note_launch();
   // look-back tables of all passes, zeroed once
   uint32_t* lookback = at<uint32_t>(ws, L.lookback);
   const int64_t lb_words = L.n_tiles_sort * kRadixBins * kRadixPasses;
@@ -1057,28 +1286,29 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
       reinterpret_cast<unsigned long long*>(lookback), (lb_words + 1) / 2); note_launch();
   prof_end(kPhKeys, s);
   prof_begin(kPhSort, s);
-  const size_t smem = sizeof(SortSmem);
-  cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const uint64_t* kin = keys_a;
+  const size_t smem = sizeof(SortSmem<kRadixBits>);
+  cudaFuncSetAttribute(k_onesweep<kRadixBits, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_onesweep<kRadixBits, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const uint64_t* kin = keys_in;
   const uint32_t* vin = nullptr;
-  uint64_t* kout = keys_b;
-  uint32_t* vout = vals_b;
+  uint32_t* vout = vals_a;
   for (int p = 0; p < kRadixPasses; ++p) {
-    k_onesweep<<<(unsigned)L.n_tiles_sort, kSortThreads, smem, s>>>(
-        kin, vin, kout, vout, n, p, lookback + (size_t)p * L.n_tiles_sort * kRadixBins, m); note_launch();
+    uint64_t* kout = (kin == keys_a) ? keys_b : keys_a;
+    uint32_t* lb = lookback + (size_t)p * L.n_tiles_sort * kRadixBins;
+    if (p + 1 < kRadixPasses) {
+      k_onesweep<kRadixBits, false><<<(unsigned)L.n_tiles_sort, kSortThreads, smem, s>>>(
+          kin, vin, kout, vout, n, p, p * kRadixBits, lb, m, nullptr, nullptr, 0, nullptr);
+    } else {  // last pass: the sorted points (gather) instead of the permutation
+      k_onesweep<kRadixBits, true><<<(unsigned)L.n_tiles_sort, kSortThreads, smem, s>>>(
+          kin, vin, kout, nullptr, n, p, p * kRadixBits, lb, m, d_a, d_b, n_a, pts);
+    }
+    note_launch();
     kin = kout;
     vin = vout;
-    kout = (kout == keys_b) ? keys_a : keys_b;
-    vout = (vout == vals_b) ? vals_a : vals_b;
+    vout = (vout == vals_a) ? vals_b : vals_a;
   }
-  // kRadixPasses is even: the sorted keys and permutation end in keys_a / vals_a
-  static_assert(kRadixPasses % 2 == 0, "sorted output must land in buffer a");
   prof_end(kPhSort, s);
-  prof_begin(kPhGather, s);
-  float4* pts = at<float4>(ws, L.pts);
-  k_gather<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(d_a, d_b, n_a, vals_a, n, pts); note_launch();
-
-  prof_end(kPhGather, s);
+  }  // integer keys
   prof_begin(kPhSplits, s);
   // plane 0: leaf splits, then n_i at every leaf split
   unsigned long long* st = at<unsigned long long>(ws, L.scan_flags);
@@ -1096,10 +1326,18 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
   for (int pass = 0; pass < (reg ? 2 : 1); ++pass) {
     if (pass == 1) regularise(0);
     k_zero_u64<<<grid_for(split_tiles, 256, sms * 8), 256, 0, s>>>(st, split_tiles); note_launch();
-    k_leaf_splits<<<(unsigned)split_tiles, kSplitThreads, 0, s>>>(
-        keys_a, n, L.nmax0, at<int32_t>(ws, L.spl[0]), L.cap_nodes[0], st, m); note_launch();
-    k_split_sizes<<<grid_for(L.cap_nodes[0] + 1, 256, sms * 16), 256, 0, s>>>(
-        keys_a, n, at<int32_t>(ws, L.spl[0]), at<int32_t>(ws, L.nsz[0]), m); note_launch();
+    if (L.float_order) {
+      k_leaf_splits<FloatLevels><<<(unsigned)split_tiles, kSplitThreads, 0, s>>>(
+          pts, n, L.nmax0, at<int32_t>(ws, L.spl[0]), L.cap_nodes[0], st, m);
+      k_split_sizes_f<<<grid_for(L.cap_nodes[0] + 1, 256, sms * 16), 256, 0, s>>>(
+          pts, n, at<int32_t>(ws, L.spl[0]), at<int32_t>(ws, L.nsz[0]), m);
+    } else {
+      k_leaf_splits<KeyLevels><<<(unsigned)split_tiles, kSplitThreads, 0, s>>>(
+          keys_a, n, L.nmax0, at<int32_t>(ws, L.spl[0]), L.cap_nodes[0], st, m);
+      k_split_sizes<<<grid_for(L.cap_nodes[0] + 1, 256, sms * 16), 256, 0, s>>>(
+          keys_a, n, at<int32_t>(ws, L.spl[0]), at<int32_t>(ws, L.nsz[0]), m);
+    }
+    note_launch(2);
   }
   // coarser planes
   int64_t nmax = L.nmax0;
@@ -1150,23 +1388,23 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
 namespace {
 
 __global__ void k_sort_prep(Meta* m) {
-  for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) (&m->radix_hist[0][0])[i] = 0;
-  if (threadIdx.x < kRadixPasses) m->tile_ctr[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < kMaxRadixPasses * kMaxRadixBins; i += blockDim.x) (&m->radix_hist[0][0])[i] = 0;
+  if (threadIdx.x < kMaxRadixPasses) m->tile_ctr[threadIdx.x] = 0;
 }
 
 // Digit histograms of the first `passes` 8-bit digits of keys.
 __global__ void __launch_bounds__(256) k_key_hist(const uint64_t* __restrict__ keys, int64_t n, int passes, Meta* m) {
-  __shared__ uint32_t sh[kRadixPasses][kRadixBins];
-  for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) (&sh[0][0])[i] = 0;
+  __shared__ uint32_t sh[kMaxRadixPasses][256];
+  for (int i = threadIdx.x; i < kMaxRadixPasses * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = keys[i];
-    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k >> (p * kRadixBits)) & (kRadixBins - 1)], 1u);
+    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k >> (p * 8)) & 255], 1u);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * kRadixBins; i += blockDim.x) {
+  for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) {
     const uint32_t v = (&sh[0][0])[i];
-    if (v) atomicAdd(&m->radix_hist[0][0] + i, v);
+    if (v) atomicAdd(&m->radix_hist[i / 256][i % 256], v);
   }
 }
 
@@ -1182,19 +1420,19 @@ void launch_sort_u64(uint64_t* k_a, uint64_t* k_b, uint32_t* v_a, uint32_t* v_b,
   const int64_t n_tiles = (n + kSortTile - 1) / kSortTile;
   k_sort_prep<<<1, 256, 0, s>>>(m); note_launch();
   k_key_hist<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(k_a, n, passes, m); note_launch();
-  k_radix_offsets<<<1, 32 * kRadixPasses, 0, s>>>(m); note_launch();
-  const int64_t lb_words = n_tiles * kRadixBins * passes;
+  k_radix_offsets<<<1, 32 * passes, 0, s>>>(m, passes, 256); note_launch();
+  const int64_t lb_words = n_tiles * 256 * passes;
   k_zero_u64<<<grid_for(lb_words / 2 + 1, 256, sms * 8), 256, 0, s>>>(
       reinterpret_cast<unsigned long long*>(lookback), (lb_words + 1) / 2); note_launch();
-  const size_t smem = sizeof(SortSmem);
-  cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = sizeof(SortSmem<8>);
+  cudaFuncSetAttribute(k_onesweep<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const uint64_t* kin = k_a;
   const uint32_t* vin = nullptr;
   uint64_t* kout = k_b;
   uint32_t* vout = v_b;
   for (int p = 0; p < passes; ++p) {
-    k_onesweep<<<(unsigned)n_tiles, kSortThreads, smem, s>>>(kin, vin, kout, vout, n, p,
-                                                             lookback + (size_t)p * n_tiles * kRadixBins, m);
+    k_onesweep<8, false><<<(unsigned)n_tiles, kSortThreads, smem, s>>>(
+        kin, vin, kout, vout, n, p, 8 * p, lookback + (size_t)p * n_tiles * 256, m, nullptr, nullptr, 0, nullptr);
     note_launch();
     kin = kout;
     vin = vout;

@@ -296,7 +296,7 @@ int launch_catalogue(const Layout& L, char* ws, float periodic_L, const float* d
                                            " bytes of interaction-list space needed)");
   const int32_t* ig_pt = at<int32_t>(ws, L.ig_pt);
   const float4* pts = at<float4>(ws, L.pts);
-  // group order: stable sort of z positions by root z position (roots < 2^30: 4 passes)
+  // group order: stable sort of z positions by root z position (roots < 2^31: 4 passes of 8 bits)
   k_cat_keys<<<cat_grid(n, 256, sms * 8), 256, 0, s>>>(ig_pt, n, k_a); note_launch();
   launch_sort_u64(k_a, k_b, v_a, v_b, n, 4, at<uint32_t>(ws, L.lookback), s, m);
   k_cat_order<<<cat_grid(n, 256, sms * 8), 256, 0, s>>>(pts, v_a, n, d_order); note_launch();

@@ -14,9 +14,14 @@ constexpr int kMaxPlanes = 14;          // planes 0..kMaxPlanes-1, plus the supe
 constexpr int kKeyBits = 21;            // per coordinate; 63-bit keys (Sec. II-A)
 constexpr int kSentinelLevel = 64;      // level of the gaps before the first / after the last point
 constexpr int kIndexLevelOffset = 32;   // equal keys: level = bit_length((i-1)^i) - 32
+// LSD radix sort of the 63-bit keys: 8 passes of 8-bit digits (9-bit digits,
+// 7 passes, measured slower: twice the digit work per tile and fewer tiles per
+// SM).  The digit tables in Meta hold up to kMaxRadixPasses x kMaxRadixBins.
 constexpr int kRadixBits = 8;
-constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kRadixBins = 1 << kRadixBits;                                   // 256
 constexpr int kRadixPasses = (3 * kKeyBits + kRadixBits - 1) / kRadixBits;  // 8
+constexpr int kMaxRadixPasses = 8;
+constexpr int kMaxRadixBins = 512;
 constexpr int kSortThreads = 256;
 constexpr int kSortIpt = 12;
 constexpr int kSortTile = kSortThreads * kSortIpt;  // 4096 keys per tile
@@ -68,8 +73,8 @@ struct Meta {
   unsigned long long fof_pairs;      // point pairs evaluated by the FoF LeafToLeaf
   unsigned long long pair_off[kMaxPlanes + 1];  // FoF: pair list of each plane in the arena
   unsigned long long pair_cnt[kMaxPlanes + 1];
-  uint32_t radix_offsets[kRadixPasses][kRadixBins];  // exclusive digit offsets per pass
-  uint32_t radix_hist[kRadixPasses][kRadixBins];     // digit histograms per pass
+  uint32_t radix_offsets[kMaxRadixPasses][kMaxRadixBins];  // exclusive digit offsets per pass
+  uint32_t radix_hist[kMaxRadixPasses][kMaxRadixBins];     // digit histograms per pass
   int32_t reg_lvl[kMaxPlanes];       // regularisation: lvl_max per plane (127 = none)
   unsigned long long vol_hist[kVolBins];  // points per node-volume class of one plane
 };
@@ -79,11 +84,13 @@ struct Layout {
   int64_t n;
   int32_t nmax0, c, n_target, ngr, heap;
   float reg_fmax;                     // 0: no regularisation
+  int32_t float_order;                // 1: float z-order (no keys; pts_tmp is the sort's second buffer)
   int32_t n_planes;
   int64_t cap_nodes[kMaxPlanes + 1];  // [n_planes] = super-node capacity
   int64_t cap_ilist;                  // entries
   int64_t n_tiles_sort;
   size_t meta, keys_a, keys_b, vals_a, vals_b, lookback, pts, scan_flags;
+  size_t pts_tmp;               // float4 [n] (float order only)
   size_t spl[kMaxPlanes + 1];   // int32 split arrays (cap_nodes+1); [n_planes] = super splits
   size_t gap[kMaxPlanes];       // int32 point-space gap index of each split
   size_t nsz[kMaxPlanes];       // int32 n_i at every split of each plane
@@ -124,6 +131,7 @@ struct Params {
   int32_t nmax0, c, n_target, ngr, heap;
   float fac_nodes, fac_ilist;
   float reg_fmax;
+  int32_t float_order;  // 1: full-precision float z-order instead of integer keys
 };
 
 // ---------------------------------------------------------------- host API

@@ -40,7 +40,7 @@ def test_workspace_bytes_grows_and_validates():
     c = jzt.workspace_bytes(1 << 27, 16)
     assert 0 < a < b < c
     assert c < 40 * (1 << 30)  # stays well inside HBM at 2^27 points
-    for bad in (0, -5, 1 << 30):
+    for bad in (0, -5, 1 << 31):
         with pytest.raises(jzt.JztError) as e:
             jzt.workspace_bytes(bad)
         assert e.value.code == jzt.JZT_ERR_INVALID

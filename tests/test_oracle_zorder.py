@@ -230,3 +230,15 @@ def test_float_tree_planes_match_the_integer_tree_on_the_grid():
         assert len(spl_i) == len(spl_f)
         assert all(np.array_equal(a, b) for a, b in zip(gaps_i, gaps_f))
         assert all(np.array_equal(a, b) for a, b in zip(spl_i, spl_f))
+
+
+def test_node_sizes_walk_equals_brute_count():
+    """The outward count of n_i (used at the sizes of the GPU tests) equals the
+    direct count over all points, on mixed-scale data with duplicates and zeros."""
+    rng = np.random.default_rng(31)
+    x = (rng.standard_normal((160, 3)) * 10.0 ** rng.uniform(-30, 30, (160, 3))).astype(np.float32)
+    x[::11] = x[5]
+    x[::13, 2] = -0.0
+    sx = x[oracle.zorder_sort(x)]
+    lvl = oracle.zorder_gap_levels(sx)
+    assert np.array_equal(oracle.zorder_node_sizes(sx, lvl), oracle.zorder_node_sizes_brute(sx, lvl))
