@@ -65,12 +65,15 @@ def parse():
     ap.add_argument("--batch-sets", type=int, default=512, help="batched sets (0 = skip the batched run)")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=1000, help="served requests (0 = skip serving)")
+    ap.add_argument("--serve-requests", type=int, default=20000, help="served requests (0 = skip serving)")
+    ap.add_argument("--serve-sample", type=int, default=2000,
+                    help="requests (the first ones of the stream) used to measure capacity and for the load sweep")
     ap.add_argument("--serve-lanes", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-load", type=float, default=0.8,
                     help="arrival rate as a fraction of the one-call server's measured capacity")
-    ap.add_argument("--serve-sweep", default="", help="comma-separated extra loads to run both servers at")
+    ap.add_argument("--serve-sweep", default="0.5,1.0,1.5",
+                    help="comma-separated extra loads to run both servers at (on the first --serve-sample requests)")
     return ap.parse_args()
 
 
@@ -214,6 +217,11 @@ def batched_run(a, dev, log):
 
     ms_batch = timed(batch.run, a.batch_steps)
     bad = [j for j, c in enumerate(batch.statuses()) if c != 0]
+    # the same batch with the kNN LeafToLeaf of all jobs in persistent launches over a
+    # device work queue (one workspace per job), also replayed from a CUDA graph
+    qbatch = jzt.Batch(sets, n_lanes=n_lanes, params=params or None, graph=True, queue=True)
+    ms_queue = timed(qbatch.run, a.batch_steps)
+    bad += [j for j, c in enumerate(qbatch.statuses()) if c != 0]
     # one call per set on one stream, one workspace sized for the largest set
     ws = jzt.alloc_workspace(max(int(st["points"].shape[0]) for st in sets), 32, None, dev)
     outs = []
@@ -235,20 +243,24 @@ def batched_run(a, dev, log):
     ms_plain = timed(one_call_per_set, a.batch_steps)
     jzt.status(ws, raise_on_error=True)
     same = True
-    for st, ob, op in zip(sets, batch.outputs, outs):
+    for st, ob, oq, op in zip(sets, batch.outputs, qbatch.outputs, outs):
         if st["op"] == "knn":
             same &= bool(torch.equal(ob[0], op[0]) and torch.equal(ob[1], op[1]))
+            same &= bool(torch.equal(oq[0], op[0]) and torch.equal(oq[1], op[1]))
         else:
-            same &= bool(torch.equal(ob, op))
+            same &= bool(torch.equal(ob, op)) and bool(torch.equal(oq, op))
     n_knn = sum(1 for st in sets if st["op"] == "knn")
     res = {"workload": f"{len(sets)} clustered sets, sizes log-uniform 1e3..2e6, seed 4",
            "points": total, "knn_sets": n_knn, "fof_sets": len(sets) - n_knn,
            "lanes": batch.n_lanes, "params": params or {}, "graph": True,
            "value": total / (ms_batch / 1000.0), "unit": "particles/s", "ms_per_batch": ms_batch,
            "one_call_per_set": {"value": total / (ms_plain / 1000.0), "ms_per_batch": ms_plain},
+           "persistent_queue": {"value": total / (ms_queue / 1000.0), "ms_per_batch": ms_queue,
+                                "form": "per-job workspaces; kNN LeafToLeaf of all jobs in one persistent launch "
+                                        "per (k class, boundary) over a device work queue; graph replay"},
            "speedup": ms_plain / ms_batch, "identical_results": same, "failed_jobs": bad,
            "steps": a.batch_steps, "autotune_s": tune_s, "generate_s": gen_s}
-    del batch, outs, ws, sets
+    del batch, qbatch, outs, ws, sets
     torch.cuda.synchronize(dev)
     torch.cuda.empty_cache()
     return res
@@ -270,11 +282,14 @@ def serving_run(a, dev, log):
     def payload(sid, n, stream):
         return workloads.clustered_device(n, seeds[sid], dev)
 
-    def requests(rate):
-        """The stream at ``rate`` requests/s (rate None: every request at t = 0)."""
+    def requests(rate, count=None):
+        """The stream at ``rate`` requests/s (rate None: every request at t = 0);
+        ``count``: only the first requests of the stream."""
         return [Request(i, r["set_id"], r["n"], r["op"], r["k"], r["b"], 1.0,
                         0.0 if rate is None else r["t_arrival"] / rate)
-                for i, r in enumerate(spec)]
+                for i, r in enumerate(spec[:count])]
+
+    sample = min(a.serve_sample, len(spec)) if a.serve_sample > 0 else len(spec)
 
     max_n = max(r["n"] for r in spec)
     plain = PlainServer(payload, max_n, device=dev)
@@ -284,7 +299,7 @@ def serving_run(a, dev, log):
     for sd in range(4):
         seeds[-1 - sd] = 99 + sd
     plain.run(warm, realtime=False)
-    cap_plain = latency_summary(plain.run(requests(None), realtime=False))
+    cap_plain = latency_summary(plain.run(requests(None, sample), realtime=False))
     rate = a.serve_load * cap_plain["requests_per_s"]
     log(f"one-call capacity {cap_plain['requests_per_s']:.1f} req/s; arrival rate {rate:.1f} req/s")
     plain_rt = latency_summary(plain.run(requests(rate), realtime=True))
@@ -292,7 +307,7 @@ def serving_run(a, dev, log):
     loads = [float(v) for v in a.serve_sweep.split(",") if v.strip()]
     for ld in loads:
         sweep[str(ld)] = {"one_call_per_request": latency_summary(
-            plain.run(requests(ld * cap_plain["requests_per_s"]), realtime=True))}
+            plain.run(requests(ld * cap_plain["requests_per_s"], sample), realtime=True))}
     del plain
     torch.cuda.empty_cache()
     srv = Server(payload, n_lanes=a.serve_lanes, hbm_budget=a.serve_budget_gb * 1e9, device=dev)
@@ -303,11 +318,11 @@ def serving_run(a, dev, log):
     peak_rt = srv.peak_used
     srv.clear()
     for ld in loads:
-        sweep[str(ld)]["served"] = latency_summary(srv.run(requests(ld * cap_plain["requests_per_s"]),
+        sweep[str(ld)]["served"] = latency_summary(srv.run(requests(ld * cap_plain["requests_per_s"], sample),
                                                            realtime=True))
         srv.clear()
     srv.stats = dict.fromkeys(srv.stats, 0)
-    cap_served = latency_summary(srv.run(requests(None), realtime=False))
+    cap_served = latency_summary(srv.run(requests(None, sample), realtime=False))
     srv.clear()
     del srv
     torch.cuda.empty_cache()
@@ -318,8 +333,9 @@ def serving_run(a, dev, log):
             "load_vs_one_call_capacity": a.serve_load, "lanes": a.serve_lanes,
             "hbm_budget_gb": a.serve_budget_gb, "served": served_rt, "served_stats": st_rt,
             "served_peak_bytes": peak_rt, "one_call_per_request": plain_rt,
-            "capacity": {"served": cap_served, "one_call_per_request": cap_plain},
-            "load_sweep": sweep or None}
+            "capacity": {"served": cap_served, "one_call_per_request": cap_plain,
+                         "requests": sample, "note": "every request of the first `requests` queued at t = 0"},
+            "load_sweep": ({"requests": sample, "loads_vs_one_call_capacity": sweep} if sweep else None)}
 
 
 def cpu_kdtree(x, n_side, k, side):

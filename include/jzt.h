@@ -248,6 +248,30 @@ int jzt_batch_run(const jzt_job *jobs, int n_jobs, const jzt_params *p,
                   void *const *d_lane_ws, const size_t *lane_ws_bytes,
                   void *const *lane_streams, int n_lanes, void *stream, int32_t *d_job_status);
 
+/* Batched jobs with the kNN LeafToLeaf of all jobs in persistent launches over a
+ * device work queue (no counterpart in the paper).  Same results as jzt_batch_run
+ * and as one jzt_knn / jzt_fof call per job.  Every job has a workspace of its own
+ * (d_job_ws[j], job_ws_bytes[j] bytes: at least jzt_workspace_bytes of that job;
+ * two jobs may not share one) because all the kNN trees must exist at once: each
+ * job's build and everything of its walk before the LeafToLeaf run on lane
+ * lane_streams[jobs[j].lane] (jobs of one lane in array order, lanes concurrently);
+ * then, on `stream`, for each class of kNN jobs with k <= 32 (k rounded up to 4,
+ * 8, 16 or 32, open or periodic boundaries) one persistent kernel pops (job, leaf)
+ * items from a device queue until every leaf of every job of the class is done.
+ * FoF jobs and kNN jobs with k > 32 run entirely on their lanes.  The lanes fork
+ * from and join back into `stream` with events, so the batch is one
+ * stream-ordered operation that can be captured into a CUDA graph.
+ * d_scratch: device memory of at least jzt_batch_queue_bytes(n_jobs) bytes,
+ * 256-byte aligned, owned by the caller (the job descriptors, the queues'
+ * leaf-count prefixes and counters live there).  d_job_status receives every
+ * job's device status code.  All arguments are validated before anything is
+ * enqueued (JZT_ERR_INVALID / _UNSUPPORTED / _WORKSPACE, the message naming the
+ * job). */
+int jzt_batch_queue_bytes(int n_jobs, size_t *bytes);
+int jzt_batch_run_queue(const jzt_job *jobs, int n_jobs, const jzt_params *p, void *const *d_job_ws,
+                        const size_t *job_ws_bytes, void *const *lane_streams, int n_lanes, void *stream,
+                        void *d_scratch, size_t scratch_bytes, int32_t *d_job_status);
+
 /* Allocation-free form of jzt_knn (the paper has no counterpart: this is for
  * callers that may not allocate device memory, e.g. code inside a framework that
  * owns all device allocations, or a real-time path that must not enter the

@@ -42,7 +42,8 @@ SYMBOLS = ("jzt_workspace_bytes", "jzt_build", "jzt_tree_knn", "jzt_tree_fof", "
            "jzt_status", "jzt_tree_arrays", "jzt_tree_plane", "jzt_tree_free", "jzt_last_error",
            "jzt_version", "jzt_profile_enable", "jzt_profile_read", "jzt_profile_phase_name",
            "jzt_knn_noalloc", "jzt_batch_run", "jzt_workspace_bytes_query", "jzt_build_query",
-           "jzt_knn_query", "jzt_tree_fof_catalogue", "jzt_selftest_wait")
+           "jzt_knn_query", "jzt_tree_fof_catalogue", "jzt_selftest_wait", "jzt_batch_queue_bytes",
+           "jzt_batch_run_queue")
 JZT_OP_KNN = 0
 JZT_OP_FOF = 1
 
@@ -106,6 +107,12 @@ def _load():
     lib.jzt_batch_run.argtypes = [ctypes.POINTER(Job), ctypes.c_int, ctypes.POINTER(Params),
                                   ctypes.POINTER(vp), ctypes.POINTER(sz), ctypes.POINTER(vp), ctypes.c_int, vp, vp]
     lib.jzt_batch_run.restype = ctypes.c_int
+    lib.jzt_batch_queue_bytes.argtypes = [ctypes.c_int, ctypes.POINTER(sz)]
+    lib.jzt_batch_queue_bytes.restype = ctypes.c_int
+    lib.jzt_batch_run_queue.argtypes = [ctypes.POINTER(Job), ctypes.c_int, ctypes.POINTER(Params),
+                                        ctypes.POINTER(vp), ctypes.POINTER(sz), ctypes.POINTER(vp), ctypes.c_int, vp,
+                                        vp, sz, vp]
+    lib.jzt_batch_run_queue.restype = ctypes.c_int
     lib.jzt_workspace_bytes_query.argtypes = [i64, i64, ctypes.c_int, ctypes.POINTER(Params), ctypes.POINTER(sz)]
     lib.jzt_build_query.argtypes = [vp, i64, vp, i64, f32, ctypes.POINTER(Params), vp, sz, vp, ctypes.POINTER(vp)]
     lib.jzt_knn_query.argtypes = [vp, i64, vp, i64, ctypes.c_int, f32, vp, vp, vp, sz, vp]
@@ -429,9 +436,13 @@ class Batch:
     Jobs are spread over ``n_lanes`` lanes by longest-processing-time order (each
     to the least loaded lane); every lane gets one workspace sized for its largest
     job.  Outputs: ``outputs[j]`` is (idx, dist2) for kNN jobs and labels for FoF.
+
+    queue=True runs the batch through jzt_batch_run_queue instead: one workspace
+    per job, and the kNN LeafToLeaf of all jobs (k <= 32) in persistent launches
+    over a device work queue (same results).
     """
 
-    def __init__(self, sets, n_lanes: int = 8, params=None, graph: bool = True, device=None):
+    def __init__(self, sets, n_lanes: int = 8, params=None, graph: bool = True, device=None, queue: bool = False):
         if not sets:
             raise ValueError("empty batch")
         dev = torch.device(device) if device is not None else sets[0]["points"].device
@@ -442,12 +453,21 @@ class Batch:
         self.n_lanes = n_lanes
         sizes = [int(s["points"].shape[0]) for s in sets]
         lane_of = assign_lanes(sizes, n_lanes)
+        self.queue = bool(queue)
         need = [0] * n_lanes
+        job_need = []
         for j, st in enumerate(sets):
             _check_xyz(st["points"])
             k = int(st.get("k", 0)) if st["op"] == "knn" else 0
-            need[lane_of[j]] = max(need[lane_of[j]], workspace_bytes(sizes[j], min(k, sizes[j]), params))
-        self.ws = [torch.empty(need[q], dtype=torch.uint8, device=dev) for q in range(n_lanes)]
+            job_need.append(workspace_bytes(sizes[j], min(k, sizes[j]), params))
+            need[lane_of[j]] = max(need[lane_of[j]], job_need[-1])
+        if self.queue:
+            self.ws = [torch.empty(b, dtype=torch.uint8, device=dev) for b in job_need]
+            qb = ctypes.c_size_t(0)
+            _check(lib.jzt_batch_queue_bytes(nj, ctypes.byref(qb)))
+            self.scratch = torch.empty(int(qb.value), dtype=torch.uint8, device=dev)
+        else:
+            self.ws = [torch.empty(need[q], dtype=torch.uint8, device=dev) for q in range(n_lanes)]
         self.streams = [torch.cuda.Stream(device=dev) for _ in range(n_lanes)]
         self.job_status = torch.zeros(nj, dtype=torch.int32, device=dev)
         self.outputs = []
@@ -470,11 +490,26 @@ class Batch:
                 self.outputs.append(lab)
             else:
                 raise ValueError(f"job {j}: op must be 'knn' or 'fof'")
-        self._ws_ptrs = (ctypes.c_void_p * n_lanes)(*[w.data_ptr() for w in self.ws])
-        self._ws_bytes = (ctypes.c_size_t * n_lanes)(*[w.numel() for w in self.ws])
+        self._ws_ptrs = (ctypes.c_void_p * len(self.ws))(*[w.data_ptr() for w in self.ws])
+        self._ws_bytes = (ctypes.c_size_t * len(self.ws))(*[w.numel() for w in self.ws])
         self._streams = (ctypes.c_void_p * n_lanes)(*[st.cuda_stream for st in self.streams])
         self.graph = None
         self._launch(torch.cuda.current_stream(dev))  # eager run (also warms up the kernels)
+        if self.queue:
+            # each job has a workspace of the default size for its N and k; the list
+            # arena is an estimate (Eq. alloc_ilist), so a job that ran out of it gets
+            # the size its status reports and the batch runs again
+            for _ in range(3):
+                grow = [j for j, c in enumerate(self.statuses()) if c == JZT_ERR_CAPACITY]
+                if not grow:
+                    break
+                for j in grow:
+                    need = status(self.ws[j])["required_bytes"]
+                    self.ws[j] = torch.empty(max(int(need * 1.25), 2 * self.ws[j].numel()), dtype=torch.uint8,
+                                             device=dev)
+                    self._ws_ptrs[j] = self.ws[j].data_ptr()
+                    self._ws_bytes[j] = self.ws[j].numel()
+                self._launch(torch.cuda.current_stream(dev))
         if graph:
             torch.cuda.synchronize(dev)
             g = torch.cuda.CUDAGraph()
@@ -483,6 +518,13 @@ class Batch:
             self.graph = g
 
     def _launch(self, stream):
+        if self.queue:
+            _check(lib.jzt_batch_run_queue(self.jobs, len(self.sets), _params(self.params), self._ws_ptrs,
+                                           self._ws_bytes, self._streams, self.n_lanes,
+                                           ctypes.c_void_p(stream.cuda_stream),
+                                           ctypes.c_void_p(self.scratch.data_ptr()), self.scratch.numel(),
+                                           ctypes.c_void_p(self.job_status.data_ptr())))
+            return
         _check(lib.jzt_batch_run(self.jobs, len(self.sets), _params(self.params), self._ws_ptrs,
                                  self._ws_bytes, self._streams, self.n_lanes,
                                  ctypes.c_void_p(stream.cuda_stream),

@@ -24,7 +24,7 @@ constexpr int kMaxRadixPasses = 8;
 constexpr int kMaxRadixBins = 512;
 constexpr int kSortThreads = 256;
 constexpr int kSortIpt = 12;
-constexpr int kSortTile = kSortThreads * kSortIpt;  // 4096 keys per tile
+constexpr int kSortTile = kSortThreads * kSortIpt;  // 3072 keys per radix-sort tile
 constexpr int kScanTile = 1024;                      // elements per compaction tile
 constexpr int kMaxK = 32;        // neighbours per LeafToLeaf pass
 constexpr int kMaxKTotal = 256;  // neighbours per query (passes of kMaxK; one walk counter each)
@@ -127,6 +127,23 @@ struct __align__(8) IEntry {
   float r2low;
 };
 
+// Everything one kNN LeafToLeaf launch needs about one tree (also one job of a
+// batch run through the device work queue).
+struct L2LArgs {
+  const float4* pts;       // source points (sorted; two point sets: the source part)
+  const NodeRec* leaves;
+  const uint2* ilo;
+  const IEntry* arena;
+  const float4* qpts;      // query points (== pts for one point set)
+  const uint2* qrange;     // per-leaf query ranges (two point sets) or null
+  int32_t* out_idx;
+  float* out_d2;
+  Meta* m;
+  int k, k_row, col0, vec_out, order;
+  float L;
+  int job;                 // index of the job in its batch (queue runs only)
+};
+
 struct Params {
   int32_t nmax0, c, n_target, ngr, heap;
   float fac_nodes, fac_ilist;
@@ -167,6 +184,16 @@ void launch_build_sets(const float* d_src, int64_t n_src, const float* d_qry, in
 // walk_knn.cu
 void launch_knn(const Layout& L, char* ws, float periodic_L, int k, int order, int32_t* d_idx,
                 float* d_d2, cudaStream_t s);
+// the kNN walk split for batches: everything before the LeafToLeaf on the job's
+// own stream, then one persistent LeafToLeaf launch per (k class, boundary)
+// over a device queue of (job, leaf) items (kmax: 4, 8, 16 or 32; k <= 32)
+void launch_knn_prepare(const Layout& L, char* ws, float periodic_L, int k, cudaStream_t s);
+void make_l2l_args(const Layout& L, char* ws, float periodic_L, int k, int32_t* d_idx, float* d_d2, int job,
+                   L2LArgs* out);
+int queue_kmax(int k);
+void launch_put_args(const L2LArgs* h_args, int n, L2LArgs* d_args, cudaStream_t s);
+void launch_knn_queue(int kmax, bool periodic, const L2LArgs* d_jobs, int n_jobs, int64_t* d_prefix,
+                      unsigned long long* d_next, int32_t* d_job_status, cudaStream_t s);
 // walk_fof.cu
 void launch_fof(const Layout& L, char* ws, float periodic_L, float b, int32_t* d_labels,
                 cudaStream_t s);
@@ -334,6 +361,59 @@ __device__ __forceinline__ bool uf_union(int32_t* p, int a, int b) {
     if (atomicCAS(p + hi, hi, lo) == hi) return true;
   }
   return false;
+}
+
+// ---- shared-memory staging by bulk copy (cp.async.bulk) with mbarriers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Bounded wait on a barrier phase; false when the budget ran out.
+// Bounded wait for the phase `parity` of an mbarrier: false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, long long limit) {
+  for (long long it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_n(bar, parity, kSpinLimit);
+}
+// Failure path: wait for a bulk copy this warp issued to land before the warp
+// leaves (a CTA must not exit while a copy still writes its shared memory).  The
+// copy reads at most 512 bytes of valid device memory, so it completes unless
+// the memory system itself has failed; the wait backs off with nanosleep and
+// still gives up after about a second rather than hang.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    if (mbar_try_wait(bar, parity)) return;
+    __nanosleep(1000);
+  }
 }
 
 #endif  // __CUDACC__

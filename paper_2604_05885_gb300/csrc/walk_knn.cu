@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -142,59 +143,6 @@ struct RHeap {
 };
 
 // ------------------------------------------------------------------ NodeToNode (kNN)
-// ---- shared-memory staging by bulk copy (cp.async.bulk) with mbarriers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// Bounded wait on a barrier phase; false when the budget ran out.
-// Bounded wait for the phase `parity` of an mbarrier: false after `limit` polls.
-__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, long long limit) {
-  for (long long it = 0; it < limit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  return mbar_wait_n(bar, parity, kSpinLimit);
-}
-// Failure path: wait for a bulk copy this warp issued to land before the warp
-// leaves (a CTA must not exit while a copy still writes its shared memory).  The
-// copy reads at most 512 bytes of valid device memory, so it completes unless
-// the memory system itself has failed; the wait backs off with nanosleep and
-// still gives up after about a second rather than hang.
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 20); ++it) {
-    if (mbar_try_wait(bar, parity)) return;
-    __nanosleep(1000);
-  }
-}
-
 constexpr int kN2NWarps = 4;
 constexpr int kMetaCap = 256;  // list entries whose metadata a warp caches in shared memory
 
@@ -921,14 +869,14 @@ __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt
   }
 }
 
-// One warp per query leaf.  Source leaves of the (sorted) interaction list are
-// staged into shared memory by bulk copies, kStages ahead of the computation;
-// the list metadata (source box and point range) is read 32 entries at a time,
-// one entry per lane.  Each query lane keeps the k smallest distances seen so
-// far in a sorted register list of floats, whose last entry is the running k-th
-// distance; every source point at or below it is buffered as a (d2, index) pair
-// in the lane's shared-memory buffer, and the exact k best (d2, index) keys are
-// selected from that buffer once the list is done.
+// One query leaf: its list's source leaves are staged into shared memory by bulk
+// copies, kStages ahead of the computation; the list metadata (source box and
+// point range) is read 32 entries at a time, one entry per lane.  Each query
+// lane keeps the k smallest distances seen so far in a sorted register list of
+// floats, whose last entry is the running k-th distance; every source point at
+// or below it is buffered as a (d2, index) pair in the lane's shared-memory
+// buffer, and the exact k best (d2, index) keys are selected from that buffer
+// once the list is done.  `broken` is set when a bounded wait gave up.
 //
 // k above 32 runs several passes (LB = true after the first): pass j fills the
 // row's columns col0 = 32 j .. col0 + k - 1 (row length k_row) with the k best
@@ -936,34 +884,20 @@ __device__ __forceinline__ void scan_leaf(const float4* __restrict__ sp, int cnt
 // (so exact ties continue in index order).  The interaction lists, built for
 // all k_row neighbours, serve every pass.
 template <int KMAX, bool PER, bool LB>
-__global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l_knn(const float4* __restrict__ pts,
-                                                           const NodeRec* __restrict__ leaves,
-                                                           const uint2* __restrict__ ilo,
-                                                           const IEntry* __restrict__ arena, int k,
-                                                           int k_row, int col0, int ctr,
-                                                           const float4* __restrict__ qpts,
-                                                           const uint2* __restrict__ qrange,
-                                                           int vec_out, float L, int order,
-                                                           int32_t* __restrict__ out_idx,
-                                                           float* __restrict__ out_d2, Meta* m) {
-  extern __shared__ __align__(16) unsigned char l2l_smem[];
-  if (warp_failed(m)) return;
-  const int w = warp_id(), lane = lane_id();
-  L2LWarpSmem<KMAX>& S = reinterpret_cast<L2LWarpSmem<KMAX>*>(l2l_smem)[w];
-  if (lane == 0) {
-    for (int t = 0; t < kStages; ++t) mbar_init(&S.bar[t], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncwarp();
-  uint32_t parity = 0;  // bit t: parity of the next completion of stage t
-  const int64_t nl = m->n_nodes[0];
+__device__ __forceinline__ void l2l_leaf(const L2LArgs& A, int64_t leaf, int64_t nl, L2LWarpSmem<KMAX>& S,
+                                         uint32_t& parity, bool& broken, int lane) {
+  const float4* __restrict__ pts = A.pts;
+  const NodeRec* __restrict__ leaves = A.leaves;
+  const uint2* __restrict__ ilo = A.ilo;
+  const IEntry* __restrict__ arena = A.arena;
+  const float4* __restrict__ qpts = A.qpts;
+  const uint2* __restrict__ qrange = A.qrange;
+  int32_t* __restrict__ out_idx = A.out_idx;
+  float* __restrict__ out_d2 = A.out_d2;
+  Meta* m = A.m;
+  const int k = A.k, k_row = A.k_row, col0 = A.col0, vec_out = A.vec_out, order = A.order;
+  const float L = A.L;
   const float invL = PER ? 1.0f / L : 0.0f;
-  bool broken = false;
-  while (!broken) {
-    int64_t leaf = 0;
-    if (lane == 0) leaf = atomicAdd(&m->tile_ctr[ctr], 1u);
-    leaf = __shfl_sync(kFull, leaf, 0);
-    if (leaf >= nl) break;
     const NodeRec me = leaves[leaf];
     // query points of the leaf: the leaf's own points, or (two point sets) its
     // query range; sources are staged from pts by the listed leaves' ranges
@@ -973,7 +907,7 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
       qfirst = (int)qr.x;
       q = (int)qr.y;
     }
-    if (q == 0) continue;
+    if (q == 0) return;
     int G = 1;
     while (G < 32 && 2 * G * q <= 32) G *= 2;
     const int qi = lane / G, sub = lane & (G - 1);
@@ -1154,6 +1088,68 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l
       }
     }
     __syncwarp();
+}
+
+// One warp per query leaf, leaves taken in order from the tree's counter `ctr`.
+template <int KMAX, bool PER, bool LB>
+__global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX)) k_l2l_knn(L2LArgs A, int ctr) {
+  extern __shared__ __align__(16) unsigned char l2l_smem[];
+  Meta* m = A.m;
+  if (warp_failed(m)) return;
+  const int w = warp_id(), lane = lane_id();
+  L2LWarpSmem<KMAX>& S = reinterpret_cast<L2LWarpSmem<KMAX>*>(l2l_smem)[w];
+  if (lane == 0) {
+    for (int t = 0; t < kStages; ++t) mbar_init(&S.bar[t], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  uint32_t parity = 0;  // bit t: parity of the next completion of stage t
+  const int64_t nl = m->n_nodes[0];
+  bool broken = false;
+  while (!broken) {
+    int64_t leaf = 0;
+    if (lane == 0) leaf = atomicAdd(&m->tile_ctr[ctr], 1u);
+    leaf = __shfl_sync(kFull, leaf, 0);
+    if (leaf >= nl) break;
+    l2l_leaf<KMAX, PER, LB>(A, leaf, nl, S, parity, broken, lane);
+  }
+}
+
+// Batches: the LeafToLeaf work of many trees (jobs of one k class and one kind
+// of boundary) as one persistent launch over a device work queue.  Item i of
+// the queue is leaf i - prefix[j] of job j, prefix[j] <= i < prefix[j + 1] (the
+// jobs' leaf counts, summed on the device once their trees exist); every warp
+// pops the next item from the shared counter until the queue is empty.  Jobs
+// whose status is already an error are passed over.
+template <int KMAX, bool PER>
+__global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX))
+    k_l2l_knn_queue(const L2LArgs* __restrict__ jobs, const int64_t* __restrict__ prefix, int n_jobs,
+                    unsigned long long* next) {
+  extern __shared__ __align__(16) unsigned char l2l_smem[];
+  const int w = warp_id(), lane = lane_id();
+  L2LWarpSmem<KMAX>& S = reinterpret_cast<L2LWarpSmem<KMAX>*>(l2l_smem)[w];
+  if (lane == 0) {
+    for (int t = 0; t < kStages; ++t) mbar_init(&S.bar[t], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  uint32_t parity = 0;
+  const int64_t total = prefix[n_jobs];
+  bool broken = false;
+  while (!broken) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(next, 1ull);
+    item = __shfl_sync(kFull, item, 0);
+    if ((int64_t)item >= total) break;
+    int lo = 0, hi = n_jobs - 1;  // the job: largest j with prefix[j] <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= (int64_t)item) lo = mid;
+      else hi = mid - 1;
+    }
+    const L2LArgs A = jobs[lo];
+    if (warp_failed(A.m)) continue;
+    l2l_leaf<KMAX, PER, false>(A, (int64_t)item - prefix[lo], prefix[lo + 1] - prefix[lo], S, parity, broken, lane);
   }
 }
 
@@ -1203,14 +1199,29 @@ void l2l_knn(const Layout& L, char* ws, int k, int k_row, int col0, int pass, fl
   // (col0 is a multiple of 32)
   const int vec_out = ((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(d2)) & 15u) == 0 &&
                       (k_row % 4) == 0;
-  k_l2l_knn<KMAX, PER, LB><<<sms * 8, 32 * kL2LWarps, smem, s>>>(
-      src, at<NodeRec>(ws, L.nodes[0]), at<uint2>(ws, L.ilo[0]), at<IEntry>(ws, L.arena), k, k_row, col0,
-      kCtrWalk + pass, qry, qrange, vec_out, pl, order, idx, d2, m); note_launch();
+  L2LArgs A;
+  A.pts = src;
+  A.leaves = at<NodeRec>(ws, L.nodes[0]);
+  A.ilo = at<uint2>(ws, L.ilo[0]);
+  A.arena = at<IEntry>(ws, L.arena);
+  A.qpts = qry;
+  A.qrange = qrange;
+  A.out_idx = idx;
+  A.out_d2 = d2;
+  A.m = m;
+  A.k = k;
+  A.k_row = k_row;
+  A.col0 = col0;
+  A.vec_out = vec_out;
+  A.order = order;
+  A.L = pl;
+  k_l2l_knn<KMAX, PER, LB><<<sms * 8, 32 * kL2LWarps, smem, s>>>(A, kCtrWalk + pass); note_launch();
 }
 
+// Everything of the kNN walk before the LeafToLeaf: the top level, the internal
+// radius bounds and NodeToNode + list sort per plane.
 template <bool PER>
-void knn_all(const Layout& L, char* ws, float pl, int k, int order, int32_t* idx, float* d2,
-             cudaStream_t s) {
+void knn_prepare(const Layout& L, char* ws, float pl, int k, cudaStream_t s) {
   Meta* m = at<Meta>(ws, L.meta);
   const int sms = 152;
   const int P = L.n_planes;
@@ -1239,6 +1250,13 @@ void knn_all(const Layout& L, char* ws, float pl, int k, int order, int32_t* idx
         at<uint2>(ws, L.ilo[p]), at<IEntry>(ws, L.arena), p, m); note_launch();
     prof_end(kPhKnnSort, s);
   }
+  k_walk_peak<<<1, 32, 0, s>>>(m); note_launch();
+}
+
+template <bool PER>
+void knn_all(const Layout& L, char* ws, float pl, int k, int order, int32_t* idx, float* d2,
+             cudaStream_t s) {
+  knn_prepare<PER>(L, ws, pl, k, s);
   prof_begin(kPhKnnL2L, s);
   if (k <= 4) l2l_knn<4, PER, false>(L, ws, k, k, 0, 0, pl, order, idx, d2, s);
   else if (k <= 8) l2l_knn<8, PER, false>(L, ws, k, k, 0, 0, pl, order, idx, d2, s);
@@ -1251,7 +1269,76 @@ void knn_all(const Layout& L, char* ws, float pl, int k, int order, int32_t* idx
       else l2l_knn<32, PER, true>(L, ws, kp, k, c0, pass, pl, order, idx, d2, s);
     }
   prof_end(kPhKnnL2L, s);
-  k_walk_peak<<<1, 32, 0, s>>>(m); note_launch();
+}
+
+// Leaf counts of the queued jobs (0 for a job whose status is an error) summed
+// into prefix[0..n]; the queue counter starts at 0.  One block.
+__global__ void __launch_bounds__(1024) k_queue_prefix(const L2LArgs* __restrict__ jobs, int n, int64_t* prefix,
+                                                       unsigned long long* next) {
+  __shared__ int64_t s_w[32];
+  __shared__ int64_t s_carry;
+  if (threadIdx.x == 0) {
+    s_carry = 0;
+    *next = 0ull;
+    prefix[0] = 0;
+  }
+  __syncthreads();
+  for (int b = 0; b < n; b += 1024) {
+    const int j = b + threadIdx.x;
+    int64_t v = 0;
+    if (j < n) {
+      const Meta* m = jobs[j].m;
+      v = failed(m) ? 0 : (int64_t)m->n_nodes[0];
+    }
+    int64_t inc = v;  // inclusive scan: warps, then warp totals
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(kFull, inc, o);
+      if (lane_id() >= o) inc += t;
+    }
+    if (lane_id() == 31) s_w[warp_id()] = inc;
+    __syncthreads();
+    if (warp_id() == 0) {
+      int64_t wv = s_w[lane_id()];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(kFull, wv, o);
+        if (lane_id() >= o) wv += t;
+      }
+      s_w[lane_id()] = wv;
+    }
+    __syncthreads();
+    const int64_t before = s_carry + (warp_id() > 0 ? s_w[warp_id() - 1] : 0);
+    if (j < n) prefix[j + 1] = before + inc;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += s_w[31];
+    __syncthreads();
+  }
+}
+
+// Status word of every queued job into the caller's job-status array.
+__global__ void k_queue_statuses(const L2LArgs* __restrict__ jobs, int n, int32_t* status) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    status[jobs[j].job] = *reinterpret_cast<const volatile int32_t*>(&jobs[j].m->status);
+}
+
+// Copies up to kArgsPerLaunch job descriptors, passed by value, to the device.
+constexpr int kArgsPerLaunch = 16;
+struct ArgsChunk {
+  L2LArgs a[kArgsPerLaunch];
+};
+__global__ void k_put_args(ArgsChunk c, int count, L2LArgs* dst) {
+  if ((int)threadIdx.x < count) dst[threadIdx.x] = c.a[threadIdx.x];
+}
+
+template <int KMAX, bool PER>
+void queue_launch(const L2LArgs* d_jobs, const int64_t* d_prefix, int n_jobs, unsigned long long* d_next,
+                  cudaStream_t s) {
+  const size_t smem = sizeof(L2LWarpSmem<KMAX>) * kL2LWarps;
+  cudaFuncSetAttribute(k_l2l_knn_queue<KMAX, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_l2l_knn_queue<KMAX, PER><<<152 * JZT_L2L_MINBLOCKS(KMAX), 32 * kL2LWarps, smem, s>>>(d_jobs, d_prefix, n_jobs,
+                                                                                        d_next);
+  note_launch();
 }
 
 }  // namespace
@@ -1296,6 +1383,66 @@ void launch_selftest_wait(const Layout& L, char* ws, int which, long long limit,
   uint32_t* flag = at<uint32_t>(ws, L.arena);
   k_selftest_reset<<<1, 32, 0, s>>>(m, flag); note_launch();
   k_selftest_wait<<<1, 32, 0, s>>>(which, limit, flag, m); note_launch();
+}
+
+void launch_knn_prepare(const Layout& L, char* ws, float periodic_L, int k, cudaStream_t s) {
+  if (periodic_L > 0.0f) knn_prepare<true>(L, ws, periodic_L, k, s);
+  else knn_prepare<false>(L, ws, 0.0f, k, s);
+}
+
+void make_l2l_args(const Layout& L, char* ws, float periodic_L, int k, int32_t* d_idx, float* d_d2, int job,
+                   L2LArgs* out) {
+  L2LArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.pts = at<float4>(ws, L.pts);
+  A.leaves = at<NodeRec>(ws, L.nodes[0]);
+  A.ilo = at<uint2>(ws, L.ilo[0]);
+  A.arena = at<IEntry>(ws, L.arena);
+  A.qpts = A.pts;
+  A.qrange = nullptr;
+  A.out_idx = d_idx;
+  A.out_d2 = d_d2;
+  A.m = at<Meta>(ws, L.meta);
+  A.k = k;
+  A.k_row = k;
+  A.col0 = 0;
+  A.vec_out = ((reinterpret_cast<uintptr_t>(d_idx) | reinterpret_cast<uintptr_t>(d_d2)) & 15u) == 0 && (k % 4) == 0;
+  A.order = 0;
+  A.L = periodic_L > 0.0f ? periodic_L : 0.0f;
+  A.job = job;
+  *out = A;
+}
+
+int queue_kmax(int k) { return k <= 4 ? 4 : (k <= 8 ? 8 : (k <= 16 ? 16 : 32)); }
+
+void launch_put_args(const L2LArgs* h_args, int n, L2LArgs* d_args, cudaStream_t s) {
+  for (int b = 0; b < n; b += kArgsPerLaunch) {
+    ArgsChunk c;
+    const int cnt = n - b < kArgsPerLaunch ? n - b : kArgsPerLaunch;
+    for (int i = 0; i < cnt; ++i) c.a[i] = h_args[b + i];
+    k_put_args<<<1, 32, 0, s>>>(c, cnt, d_args + b);
+    note_launch();
+  }
+}
+
+void launch_knn_queue(int kmax, bool periodic, const L2LArgs* d_jobs, int n_jobs, int64_t* d_prefix,
+                      unsigned long long* d_next, int32_t* d_job_status, cudaStream_t s) {
+  if (n_jobs <= 0) return;
+  k_queue_prefix<<<1, 1024, 0, s>>>(d_jobs, n_jobs, d_prefix, d_next); note_launch();
+  prof_begin(kPhKnnL2L, s);
+  if (periodic) {
+    if (kmax == 4) queue_launch<4, true>(d_jobs, d_prefix, n_jobs, d_next, s);
+    else if (kmax == 8) queue_launch<8, true>(d_jobs, d_prefix, n_jobs, d_next, s);
+    else if (kmax == 16) queue_launch<16, true>(d_jobs, d_prefix, n_jobs, d_next, s);
+    else queue_launch<32, true>(d_jobs, d_prefix, n_jobs, d_next, s);
+  } else {
+    if (kmax == 4) queue_launch<4, false>(d_jobs, d_prefix, n_jobs, d_next, s);
+    else if (kmax == 8) queue_launch<8, false>(d_jobs, d_prefix, n_jobs, d_next, s);
+    else if (kmax == 16) queue_launch<16, false>(d_jobs, d_prefix, n_jobs, d_next, s);
+    else queue_launch<32, false>(d_jobs, d_prefix, n_jobs, d_next, s);
+  }
+  prof_end(kPhKnnL2L, s);
+  k_queue_statuses<<<(n_jobs + 255) / 256, 256, 0, s>>>(d_jobs, n_jobs, d_job_status); note_launch();
 }
 
 void launch_knn(const Layout& L, char* ws, float periodic_L, int k, int order, int32_t* d_idx,

@@ -1,6 +1,7 @@
-"""Batched jobs (jzt_batch_run): every job's result equals the one-call result
-of the same set (jzt_knn / jzt_fof), eagerly and replayed from a CUDA graph,
-and small jobs also match the oracle."""
+"""Batched jobs (jzt_batch_run, and jzt_batch_run_queue with the kNN LeafToLeaf
+of all jobs in persistent launches over a device work queue): every job's result
+equals the one-call result of the same set (jzt_knn / jzt_fof), eagerly and
+replayed from a CUDA graph, and small jobs also match the oracle."""
 import numpy as np
 import pytest
 
@@ -28,12 +29,17 @@ def _sets(n_sets=24, seed=5):
     return sets
 
 
+@pytest.mark.parametrize("queue", [False, True])
 @pytest.mark.parametrize("graph", [False, True])
 @pytest.mark.parametrize("n_lanes", [1, 5])
-def test_batch_matches_one_call(graph, n_lanes):
+def test_batch_matches_one_call(graph, n_lanes, queue):
     import paper_2604_05885_gb300 as jzt
     sets = _sets()
-    b = jzt.Batch(sets, n_lanes=n_lanes, graph=graph)
+    if queue:  # every k class and both boundaries in the queue; one k > 32 job on its lane
+        x = workloads.clustered(4000, 77, n_blobs=2)
+        sets += [dict(points=to_dev(x), host=x, op="knn", k=k, periodic_L=L)
+                 for k, L in ((3, 0.0), (5, 1.0), (12, 0.0), (40, 1.0))]
+    b = jzt.Batch(sets, n_lanes=n_lanes, graph=graph, queue=queue)
     for _ in range(2):
         b.run()
         assert b.statuses() == [0] * len(sets)
@@ -47,10 +53,11 @@ def test_batch_matches_one_call(graph, n_lanes):
                 assert np.array_equal(out.cpu().numpy(), rl.cpu().numpy())
 
 
-def test_batch_small_jobs_match_oracle():
+@pytest.mark.parametrize("queue", [False, True])
+def test_batch_small_jobs_match_oracle(queue):
     import paper_2604_05885_gb300 as jzt
     sets = [s for s in _sets(16, 9) if s["points"].shape[0] <= 3000]
-    b = jzt.Batch(sets, n_lanes=3, graph=True)
+    b = jzt.Batch(sets, n_lanes=3, graph=True, queue=queue)
     b.run()
     assert b.statuses() == [0] * len(sets)
     for st, out in zip(sets, b.outputs):
@@ -69,3 +76,30 @@ def test_batch_rejects_bad_job():
     x = to_dev(workloads.uniform(10, 1))
     with pytest.raises(jzt.JztError):
         jzt.Batch([dict(points=x, op="knn", k=11)], n_lanes=1, graph=False)
+
+
+def test_queue_rejects_shared_workspace_and_small_scratch():
+    import ctypes
+    import torch
+    import paper_2604_05885_gb300 as jzt
+    x = to_dev(workloads.uniform(500, 2))
+    idx = torch.empty((500, 8), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((500, 8), dtype=torch.float32, device="cuda")
+    jobs = (jzt.Job * 2)()
+    for J in jobs:
+        J.d_xyz, J.n, J.periodic_L, J.op, J.k, J.lane = x.data_ptr(), 500, 1.0, jzt.JZT_OP_KNN, 8, 0
+        J.d_idx, J.d_dist2 = idx.data_ptr(), d2.data_ptr()
+    ws = jzt.alloc_workspace(500, 8)
+    ptrs = (ctypes.c_void_p * 2)(ws.data_ptr(), ws.data_ptr())
+    sizes = (ctypes.c_size_t * 2)(ws.numel(), ws.numel())
+    streams = (ctypes.c_void_p * 1)(torch.cuda.current_stream().cuda_stream)
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
+    qb = ctypes.c_size_t(0)
+    assert jzt.lib.jzt_batch_queue_bytes(2, ctypes.byref(qb)) == 0
+    scratch = torch.empty(int(qb.value), dtype=torch.uint8, device="cuda")
+    rc = jzt.lib.jzt_batch_run_queue(jobs, 2, None, ptrs, sizes, streams, 1, None, scratch.data_ptr(),
+                                     scratch.numel(), st.data_ptr())
+    assert rc == jzt.JZT_ERR_INVALID and b"workspace of its own" in jzt.lib.jzt_last_error()
+    rc = jzt.lib.jzt_batch_run_queue(jobs, 1, None, ptrs, sizes, streams, 1, None, scratch.data_ptr(), 16,
+                                     st.data_ptr())
+    assert rc == jzt.JZT_ERR_WORKSPACE
