@@ -34,9 +34,9 @@ FP32_LANES_PER_SM = 128
 SMS = 152
 SORT_BYTES_PER_PT = 24    # one LSD pass: read key+value, write key+value (8+4 each way)
 BUILD_FLOOR_BYTES = 42    # read xyz 12 + sorted float4 16 + keys/perm 12 + tree ~2
-# DRAM bytes per point of one k_l2l_knn launch (k = 16): 695 MB read + 2094 MB written
+# DRAM bytes per point of one k_l2l_knn launch (k = 16): 693 MB read + 2098 MB written
 # on 2^24 points, from the ncu capture of this kernel version
-L2L_TRAFFIC_BYTES_PER_PT = (693.7e6 + 2097.7e6) / (1 << 24)
+L2L_TRAFFIC_BYTES_PER_PT = (693.2e6 + 2097.7e6) / (1 << 24)
 
 
 def parse():
