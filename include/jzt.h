@@ -86,7 +86,7 @@ typedef struct jzt_status_info {
     int64_t knn_pairs;        /* point pairs evaluated by the last kNN LeafToLeaf */
     int64_t fof_pairs;        /* point pairs evaluated by the last FoF LeafToLeaf */
     int64_t knn_stats[8];     /* last kNN LeafToLeaf: [0] list entries examined, [1] source
-                                 leaves scanned, [2] candidates queued, [3] heap insertions */
+                                 leaves scanned, [2] candidates queued; [3..7] reserved (0) */
     int64_t knn_plane_entries[16];  /* last kNN walk: interaction-list entries per plane */
 } jzt_status_info;
 

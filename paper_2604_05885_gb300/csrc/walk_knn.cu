@@ -698,6 +698,23 @@ __device__ __forceinline__ void merge_distances(uint2 (*buf)[32], Cand<KMAX>& C,
   C.thr = act ? C.F.t[KMAX - 1] : -INFINITY;
 }
 
+// Descending bitonic sort of N keys in registers (N a power of two).
+template <int N>
+__device__ __forceinline__ void sort_desc(unsigned long long (&v)[N]) {
+#pragma unroll
+  for (int size = 2; size <= N; size <<= 1)
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1)
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int j = i ^ stride;
+        if (j > i) {
+          if ((i & size) == 0) cswap(v[j], v[i]);  // this block descending: the larger first
+          else cswap(v[i], v[j]);
+        }
+      }
+}
+
 // Exact selection of the k best (d2, index) keys of a lane's buffer.
 template <int KMAX>
 __device__ __forceinline__ void select_exact(uint2 (*buf)[32], int nb, int k, int lane,
@@ -1039,18 +1056,70 @@ __device__ __forceinline__ void l2l_leaf(const L2LArgs& A, int64_t leaf, int64_t
     // entries beyond it, exact (d2, index) selection
     merge_distances<KMAX>(S.buf, C, lane, act);
     compact<KMAX>(S.buf, C, k, lane);
-    RegTopK<unsigned long long, KMAX> T;
-    select_exact<KMAX>(S.buf, C.nb, k, lane, T);
-    __syncwarp();
-    // merge the G partial lists of each query (butterfly over the sub-lanes)
-    for (int st = 1; st < G; st <<= 1) {
-      unsigned long long pb[KMAX];
+    // one lane per query: after the compaction the buffer holds at most KMAX
+    // entries, the k best among them; one descending sorting network puts them,
+    // smallest last, in the last k slots (pads of kKeyInf in front), and the row
+    // is written straight from the network's registers
+    if (G == 1) {
+      unsigned long long v[KMAX];
 #pragma unroll
-      for (int e = 0; e < KMAX; ++e) pb[e] = __shfl_xor_sync(kFull, T.t[e], st);
-      // the partner's pads (0) are not candidates: lift them out of the way
+      for (int i = 0; i < KMAX; ++i) {
+        const uint2 e = S.buf[i][lane];
+        v[i] = i < C.nb ? (((unsigned long long)e.x << 32) | (e.y + 1u)) : kKeyInf;
+      }
+      sort_desc<KMAX>(v);
+      if (act && !broken) {
+        const int64_t row = order == 0 ? (int64_t)__float_as_int(qp.w) : (int64_t)(qfirst + qi);
+        int32_t* oi = out_idx + row * k_row + col0;
+        float* od = out_d2 + row * k_row + col0;
+        if (vec_out && k == KMAX) {  // whole rows as 16-byte stores; j-th best in v[KMAX - 1 - j]
 #pragma unroll
-      for (int e = 0; e < KMAX; ++e) pb[e] = pb[e] == 0ull ? kKeyInf : pb[e];
-      T.template merge<KMAX>(pb);
+          for (int e = 0; e < KMAX; e += 4) {
+            const unsigned long long a0 = v[KMAX - 1 - e], a1 = v[KMAX - 2 - e], a2 = v[KMAX - 3 - e],
+                                     a3 = v[KMAX - 4 - e];
+            reinterpret_cast<int4*>(oi)[e / 4] =
+                make_int4((int32_t)(uint32_t)(a0 & 0xffffffffull) - 1, (int32_t)(uint32_t)(a1 & 0xffffffffull) - 1,
+                          (int32_t)(uint32_t)(a2 & 0xffffffffull) - 1, (int32_t)(uint32_t)(a3 & 0xffffffffull) - 1);
+            reinterpret_cast<float4*>(od)[e / 4] =
+                make_float4(__uint_as_float((uint32_t)(a0 >> 32)), __uint_as_float((uint32_t)(a1 >> 32)),
+                            __uint_as_float((uint32_t)(a2 >> 32)), __uint_as_float((uint32_t)(a3 >> 32)));
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < KMAX; ++e) {
+            if (e >= KMAX - k) {
+              oi[KMAX - 1 - e] = (int32_t)(uint32_t)(v[e] & 0xffffffffull) - 1;
+              od[KMAX - 1 - e] = __uint_as_float((uint32_t)(v[e] >> 32));
+            }
+          }
+        }
+      }
+    } else {
+      RegTopK<unsigned long long, KMAX> T;
+      select_exact<KMAX>(S.buf, C.nb, k, lane, T);
+      __syncwarp();
+      // merge the G partial lists of each query (butterfly over the sub-lanes)
+      for (int st = 1; st < G; st <<= 1) {
+        unsigned long long pb[KMAX];
+#pragma unroll
+        for (int e = 0; e < KMAX; ++e) pb[e] = __shfl_xor_sync(kFull, T.t[e], st);
+        // the partner's pads (0) are not candidates: lift them out of the way
+#pragma unroll
+        for (int e = 0; e < KMAX; ++e) pb[e] = pb[e] == 0ull ? kKeyInf : pb[e];
+        T.template merge<KMAX>(pb);
+      }
+      if (act && sub == 0 && !broken) {
+        const int64_t row = order == 0 ? (int64_t)__float_as_int(qp.w) : (int64_t)(qfirst + qi);
+        int32_t* oi = out_idx + row * k_row + col0;
+        float* od = out_d2 + row * k_row + col0;
+#pragma unroll
+        for (int e = 0; e < KMAX; ++e) {
+          if (e >= KMAX - k) {
+            oi[e - (KMAX - k)] = (int32_t)(uint32_t)(T.t[e] & 0xffffffffull) - 1;
+            od[e - (KMAX - k)] = __uint_as_float((uint32_t)(T.t[e] >> 32));
+          }
+        }
+      }
     }
     if (lane == 0 && pairs) {
       atomicAdd(&m->knn_pairs, pairs);
@@ -1062,30 +1131,6 @@ __device__ __forceinline__ void l2l_leaf(const L2LArgs& A, int64_t leaf, int64_t
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(kFull, a, o);
       if (lane == 0) atomicAdd(&m->knn_stats[2], a);
-    }
-    if (act && sub == 0 && !broken) {
-      const int64_t row = order == 0 ? (int64_t)__float_as_int(qp.w) : (int64_t)(qfirst + qi);
-      int32_t* oi = out_idx + row * k_row + col0;
-      float* od = out_d2 + row * k_row + col0;
-      if (vec_out && k == KMAX) {  // whole rows as 16-byte stores (aligned rows, k a multiple of 4)
-#pragma unroll
-        for (int e = 0; e < KMAX; e += 4) {
-          reinterpret_cast<int4*>(oi)[e / 4] =
-              make_int4((int32_t)(uint32_t)(T.t[e] & 0xffffffffull) - 1, (int32_t)(uint32_t)(T.t[e + 1] & 0xffffffffull) - 1,
-                        (int32_t)(uint32_t)(T.t[e + 2] & 0xffffffffull) - 1, (int32_t)(uint32_t)(T.t[e + 3] & 0xffffffffull) - 1);
-          reinterpret_cast<float4*>(od)[e / 4] =
-              make_float4(__uint_as_float((uint32_t)(T.t[e] >> 32)), __uint_as_float((uint32_t)(T.t[e + 1] >> 32)),
-                          __uint_as_float((uint32_t)(T.t[e + 2] >> 32)), __uint_as_float((uint32_t)(T.t[e + 3] >> 32)));
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < KMAX; ++e) {
-          if (e >= KMAX - k) {
-            oi[e - (KMAX - k)] = (int32_t)(uint32_t)(T.t[e] & 0xffffffffull) - 1;
-            od[e - (KMAX - k)] = __uint_as_float((uint32_t)(T.t[e] >> 32));
-          }
-        }
-      }
     }
     __syncwarp();
 }
