@@ -36,7 +36,7 @@ SORT_BYTES_PER_PT = 24    # one LSD pass: read key+value, write key+value (8+4 e
 BUILD_FLOOR_BYTES = 42    # read xyz 12 + sorted float4 16 + keys/perm 12 + tree ~2
 # DRAM bytes per point of one k_l2l_knn launch (k = 16): 693 MB read + 2098 MB written
 # on 2^24 points, from the ncu capture of this kernel version
-L2L_TRAFFIC_BYTES_PER_PT = (693.2e6 + 2097.7e6) / (1 << 24)
+L2L_TRAFFIC_BYTES_PER_PT = (692.6e6 + 2098.0e6) / (1 << 24)
 
 
 def parse():
@@ -195,11 +195,12 @@ def batched_run(a, dev, log):
     total = sum(int(st["points"].shape[0]) for st in sets)
     t = time.perf_counter()
     if a.no_autotune:
-        n_lanes, params = 8, {}
+        n_lanes, params, caps = 8, {}, [0, 0, 0]
     else:
-        n_lanes, params = autotune.tune(sets, cache=os.path.join(a.cache, "autotune.json"), log=log)
+        n_lanes, params, caps = autotune.tune(sets, cache=os.path.join(a.cache, "autotune.json"), log=log)
+    cap_fn = autotune.leaf_cap_fn(caps)
     tune_s = time.perf_counter() - t
-    batch = jzt.Batch(sets, n_lanes=n_lanes, params=params or None, graph=True)
+    batch = jzt.Batch(sets, n_lanes=n_lanes, params=params or None, graph=True, nmax0_of=cap_fn)
     stream = torch.cuda.current_stream(dev)
 
     def timed(fn, steps):
@@ -219,7 +220,7 @@ def batched_run(a, dev, log):
     bad = [j for j, c in enumerate(batch.statuses()) if c != 0]
     # the same batch with the kNN LeafToLeaf of all jobs in persistent launches over a
     # device work queue (one workspace per job), also replayed from a CUDA graph
-    qbatch = jzt.Batch(sets, n_lanes=n_lanes, params=params or None, graph=True, queue=True)
+    qbatch = jzt.Batch(sets, n_lanes=n_lanes, params=params or None, graph=True, queue=True, nmax0_of=cap_fn)
     ms_queue = timed(qbatch.run, a.batch_steps)
     bad += [j for j, c in enumerate(qbatch.statuses()) if c != 0]
     # one call per set on one stream, one workspace sized for the largest set
@@ -253,6 +254,8 @@ def batched_run(a, dev, log):
     res = {"workload": f"{len(sets)} clustered sets, sizes log-uniform 1e3..2e6, seed 4",
            "points": total, "knn_sets": n_knn, "fof_sets": len(sets) - n_knn,
            "lanes": batch.n_lanes, "params": params or {}, "graph": True,
+           "leaf_capacity_per_size_class": {"N < 2^14": caps[0] or "params", "2^14 <= N < 2^18": caps[1] or "params",
+                                            "N >= 2^18": caps[2] or "params"},
            "value": total / (ms_batch / 1000.0), "unit": "particles/s", "ms_per_batch": ms_batch,
            "one_call_per_set": {"value": total / (ms_plain / 1000.0), "ms_per_batch": ms_plain},
            "persistent_queue": {"value": total / (ms_queue / 1000.0), "ms_per_batch": ms_queue,

@@ -226,7 +226,8 @@ typedef struct jzt_job {
     int32_t k;            /* kNN: neighbours per point, 1..min(256, N) */
     float b;              /* FoF: linking length */
     int32_t lane;         /* lane (0 <= lane < n_lanes) that runs the job */
-    int32_t pad;
+    int32_t nmax0;        /* this job's leaf capacity N_max^(0), 1..32; 0 = that of the batch's params
+                             (results never depend on it; an autotuner picks it per set size) */
     int32_t *d_idx;       /* kNN output, N x k (input order), as jzt_tree_knn */
     float *d_dist2;       /* kNN output, N x k */
     int32_t *d_labels;    /* FoF output, N, as jzt_tree_fof */

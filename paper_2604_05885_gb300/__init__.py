@@ -67,7 +67,7 @@ class Job(ctypes.Structure):
     """Mirror of jzt_job."""
     _fields_ = [("d_xyz", ctypes.c_void_p), ("n", ctypes.c_int64), ("periodic_L", ctypes.c_float),
                 ("op", ctypes.c_int32), ("k", ctypes.c_int32), ("b", ctypes.c_float), ("lane", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("d_idx", ctypes.c_void_p), ("d_dist2", ctypes.c_void_p),
+                ("nmax0", ctypes.c_int32), ("d_idx", ctypes.c_void_p), ("d_dist2", ctypes.c_void_p),
                 ("d_labels", ctypes.c_void_p)]
 
 
@@ -440,9 +440,13 @@ class Batch:
     queue=True runs the batch through jzt_batch_run_queue instead: one workspace
     per job, and the kNN LeafToLeaf of all jobs (k <= 32) in persistent launches
     over a device work queue (same results).
+
+    nmax0_of: optional callable N -> leaf capacity N_max^(0) (1..32, 0 = params')
+    giving each job its own leaf capacity by its size (see autotune.tune).
     """
 
-    def __init__(self, sets, n_lanes: int = 8, params=None, graph: bool = True, device=None, queue: bool = False):
+    def __init__(self, sets, n_lanes: int = 8, params=None, graph: bool = True, device=None, queue: bool = False,
+                 nmax0_of=None):
         if not sets:
             raise ValueError("empty batch")
         dev = torch.device(device) if device is not None else sets[0]["points"].device
@@ -454,12 +458,16 @@ class Batch:
         sizes = [int(s["points"].shape[0]) for s in sets]
         lane_of = assign_lanes(sizes, n_lanes)
         self.queue = bool(queue)
+        self.job_nmax0 = [int(nmax0_of(n)) if nmax0_of else 0 for n in sizes]
         need = [0] * n_lanes
         job_need = []
         for j, st in enumerate(sets):
             _check_xyz(st["points"])
             k = int(st.get("k", 0)) if st["op"] == "knn" else 0
-            job_need.append(workspace_bytes(sizes[j], min(k, sizes[j]), params))
+            pj = dict(params or {})
+            if self.job_nmax0[j]:
+                pj["nmax0"] = self.job_nmax0[j]
+            job_need.append(workspace_bytes(sizes[j], min(k, sizes[j]), pj or None))
             need[lane_of[j]] = max(need[lane_of[j]], job_need[-1])
         if self.queue:
             self.ws = [torch.empty(b, dtype=torch.uint8, device=dev) for b in job_need]
@@ -478,6 +486,7 @@ class Batch:
             J.n = sizes[j]
             J.periodic_L = float(st.get("periodic_L", 0.0))
             J.lane = lane_of[j]
+            J.nmax0 = self.job_nmax0[j]
             if st["op"] == "knn":
                 k = int(st["k"])
                 idx = torch.empty((sizes[j], k), dtype=torch.int32, device=dev)

@@ -55,7 +55,12 @@ int validate_jobs(const jzt_job* jobs, int n_jobs, const Params& P, int n_lanes,
     } else {
       return fail_msg(JZT_ERR_INVALID, tag + "op must be JZT_OP_KNN or JZT_OP_FOF");
     }
-    compute_layout(J.n, P, 0, bytes_of(j), &lay[(size_t)j]);
+    Params Pj = P;  // the job's own leaf capacity, if it has one
+    if (J.nmax0 != 0) {
+      if (J.nmax0 < 1 || J.nmax0 > 32) return fail_msg(JZT_ERR_INVALID, tag + "nmax0 must be 0 or in 1..32");
+      Pj.nmax0 = J.nmax0;
+    }
+    compute_layout(J.n, Pj, 0, bytes_of(j), &lay[(size_t)j]);
     if (lay[(size_t)j].cap_ilist < 0) return fail_msg(JZT_ERR_WORKSPACE, tag + "workspace too small");
   }
   return JZT_OK;

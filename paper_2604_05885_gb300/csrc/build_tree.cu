@@ -445,19 +445,23 @@ __global__ void __launch_bounds__(kSortThreads, 3)
   uint64_t key[kSortIpt];
   uint32_t val[kSortIpt];
   uint32_t rank[kSortIpt];
-  const int64_t wbase = base + (int64_t)w * (32 * kSortIpt);
+  uint32_t dig[kSortIpt];
+  // key i of this thread sits at tile offset lofs + 32 i (striped over the warp)
+  const int lofs = w * (32 * kSortIpt) + lane;
+  const uint64_t* __restrict__ kp = kin + base + lofs;
+  const uint32_t* __restrict__ vp = vin ? vin + base + lofs : nullptr;
 #pragma unroll
   for (int i = 0; i < kSortIpt; ++i) {
-    const int64_t idx = wbase + i * 32 + lane;
-    const bool ok = idx < n;
-    key[i] = ok ? kin[idx] : 0ull;
-    val[i] = ok ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
+    const bool ok = lofs + i * 32 < tile_n;
+    key[i] = ok ? kp[i * 32] : 0ull;
+    val[i] = ok ? (vp ? vp[i * 32] : (uint32_t)(base + lofs + i * 32)) : 0u;
+    dig[i] = (uint32_t)(key[i] >> shift) & (kBins - 1);
   }
   const unsigned lt = lanemask_lt();
 #pragma unroll
   for (int i = 0; i < kSortIpt; ++i) {
-    const bool valid = wbase + i * 32 + lane < n;
-    const uint32_t d = (uint32_t)(key[i] >> shift) & (kBins - 1);
+    const bool valid = lofs + i * 32 < tile_n;
+    const uint32_t d = dig[i];
     unsigned peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
     for (int b = 0; b < BITS; ++b) {
@@ -507,8 +511,8 @@ __global__ void __launch_bounds__(kSortThreads, 3)
   // keys into shared memory in digit order
 #pragma unroll
   for (int i = 0; i < kSortIpt; ++i) {
-    if (wbase + i * 32 + lane < n) {
-      const uint32_t d = (uint32_t)(key[i] >> shift) & (kBins - 1);
+    if (lofs + i * 32 < tile_n) {
+      const uint32_t d = dig[i];
       const uint32_t pos = S.tile_start[d] + S.whist[w][d] + rank[i];
       S.stage_k[pos] = key[i];
       S.stage_v[pos] = val[i];

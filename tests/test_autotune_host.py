@@ -17,12 +17,17 @@ def fake_tuner(monkeypatch):
     from paper_2604_05885_gb300 import autotune
 
     class FakeBatch:
-        def __init__(self, sets, n_lanes, params=None, graph=True):
+        def __init__(self, sets, n_lanes, params=None, graph=True, nmax0_of=None):
             self.n_lanes, self.params = n_lanes, dict(params or {})
+            # the leaf capacity of each size class, read at one size per class
+            self.caps = tuple(nmax0_of(n) if nmax0_of else 0 for n in (1000, 100_000, 1_000_000))
 
     cost = {}  # (lanes, sorted params) -> ms; anything unlisted is slow
+    # (leaf capacity per size class) -> ms for the per-class trials; unlisted: slow
 
     def fake_time(batch, reps):
+        if batch.caps != (0, 0, 0):
+            return cost.get(("caps", batch.caps), 100.0)
         return cost.get((batch.n_lanes, tuple(sorted(batch.params.items()))), 100.0)
 
     monkeypatch.setattr(autotune, "Batch", FakeBatch)
@@ -39,9 +44,10 @@ def test_fastest_configuration_wins_and_is_cached(fake_tuner, tmp_path):
     sets = _sets([(1000, "knn", 8), (3000, "fof", 0), (70000, "knn", 16)])
     cache = str(tmp_path / "tune.json")
     seen = []
-    lanes, params = autotune.tune(sets, cache=cache, log=seen.append)
-    assert (lanes, params) == (8, {"n_target": 250})
-    assert len(seen) == len(autotune.LANES) * len(autotune.PARAMS)  # every candidate timed once
+    lanes, params, caps = autotune.tune(sets, cache=cache, log=seen.append)
+    assert (lanes, params, caps) == (8, {"n_target": 250}, [0, 0, 0])
+    # every (lanes, params) candidate timed once, then 16 and 24 for the two size classes present
+    assert len(seen) == len(autotune.LANES) * len(autotune.PARAMS) + 2 * 2
     table = json.load(open(cache))
     entry = table[autotune.signature(sets)]
     assert entry["n_lanes"] == 8 and entry["params"] == {"n_target": 250} and entry["ms"] == 3.0
@@ -58,7 +64,7 @@ def test_cached_entry_is_used_without_timing(fake_tuner, tmp_path, monkeypatch):
         raise AssertionError("a cached signature must not be timed again")
 
     monkeypatch.setattr(autotune, "_time", no_timing)
-    assert autotune.tune(sets, cache=cache) == first == (4, {"ngr": 16})
+    assert autotune.tune(sets, cache=cache) == first == (4, {"ngr": 16}, [0, 0, 0])
 
 
 def test_signature_groups_by_operation_and_size_octave(fake_tuner):
@@ -71,3 +77,18 @@ def test_signature_groups_by_operation_and_size_octave(fake_tuner):
     assert a == b
     assert len({a, c, d, e}) == 4
     assert a.startswith("FakeGPU|2|")
+
+
+def test_leaf_capacity_per_size_class(fake_tuner, tmp_path):
+    """After the grid search the tuner tries a leaf capacity per size class, one class at
+    a time, keeping what is faster; size classes follow N."""
+    autotune, cost = fake_tuner
+    cost[(16, ())] = 3.0
+    cost[("caps", (16, 0, 0))] = 2.0      # small sets faster with 16-point leaves
+    cost[("caps", (16, 0, 24))] = 2.5     # slower than the kept (16, 0, 0)
+    sets = _sets([(1000, "knn", 8), (500_000, "fof", 0)])
+    lanes, params, caps = autotune.tune(sets, cache=str(tmp_path / "t.json"))
+    assert (lanes, params, caps) == (16, {}, [16, 0, 0])
+    fn = autotune.leaf_cap_fn(caps)
+    assert (fn(100), fn((1 << 14) - 1), fn(1 << 14), fn(1 << 20)) == (16, 16, 0, 0)
+    assert [autotune.size_class(n) for n in (1, (1 << 14) - 1, 1 << 14, (1 << 18) - 1, 1 << 18)] == [0, 0, 1, 1, 2]

@@ -103,3 +103,24 @@ def test_queue_rejects_shared_workspace_and_small_scratch():
     rc = jzt.lib.jzt_batch_run_queue(jobs, 1, None, ptrs, sizes, streams, 1, None, scratch.data_ptr(), 16,
                                      st.data_ptr())
     assert rc == jzt.JZT_ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("queue", [False, True])
+def test_per_job_leaf_capacity_leaves_results_unchanged(queue):
+    """Each job may carry its own leaf capacity (chosen by size class); the rows and
+    labels stay those of one call per set with the default tree."""
+    import paper_2604_05885_gb300 as jzt
+    from paper_2604_05885_gb300 import autotune
+    sets = _sets(12, 21)
+    b = jzt.Batch(sets, n_lanes=3, graph=True, queue=queue, nmax0_of=autotune.leaf_cap_fn([8, 16, 24]))
+    assert sorted(set(b.job_nmax0)) == sorted({autotune.leaf_cap_fn([8, 16, 24])(int(s["points"].shape[0]))
+                                                for s in sets})
+    b.run()
+    assert b.statuses() == [0] * len(sets)
+    for st, out in zip(sets, b.outputs):
+        if st["op"] == "knn":
+            ri, rd = jzt.knn(st["points"], st["k"], st["periodic_L"])
+            assert np.array_equal(out[0].cpu().numpy(), ri.cpu().numpy())
+            assert np.array_equal(out[1].cpu().numpy(), rd.cpu().numpy())
+        else:
+            assert np.array_equal(out.cpu().numpy(), jzt.fof(st["points"], st["b"], st["periodic_L"]).cpu().numpy())
