@@ -593,8 +593,8 @@ constexpr int kL2LWarps = 4;
 constexpr int kStages = JZT_L2L_STAGES;  // source leaves in flight per warp
 
 // Exact keys are packed as (float32 bits of d2) << 32 | (original index + 1):
-// for d2 >= 0 the unsigned order of the key is the order by (d2, index), and 0
-// is below every real key (used to pad lists for k below the list size).
+// for d2 >= 0 the unsigned order of the key is the order by (d2, index);
+// kKeyInf, above every real key, pads the sorting networks.
 constexpr unsigned long long kKeyInf = ~0ull;
 
 // Per-warp shared memory: staged source leaves and, per lane, a buffer of
@@ -713,26 +713,6 @@ __device__ __forceinline__ void sort_desc(unsigned long long (&v)[N]) {
           else cswap(v[i], v[j]);
         }
       }
-}
-
-// Exact selection of the k best (d2, index) keys of a lane's buffer.
-template <int KMAX>
-__device__ __forceinline__ void select_exact(uint2 (*buf)[32], int nb, int k, int lane,
-                                             RegTopK<unsigned long long, KMAX>& T) {
-  T.init(k, 0ull, kKeyInf);
-  int mx = nb;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
-  for (int r = 0; r < mx; r += 8) {
-    unsigned long long b[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int i = r + t < nb ? r + t : 0;
-      const uint2 e = buf[i < L2LWarpSmem<KMAX>::kCap ? i : 0][lane];
-      b[t] = r + t < nb ? ((unsigned long long)e.x << 32) | (e.y + 1u) : kKeyInf;
-    }
-    T.template merge<8>(b);
-  }
 }
 
 // Keep only the buffer entries at or below thr.  If a lane still holds more
@@ -1056,18 +1036,17 @@ __device__ __forceinline__ void l2l_leaf(const L2LArgs& A, int64_t leaf, int64_t
     // entries beyond it, exact (d2, index) selection
     merge_distances<KMAX>(S.buf, C, lane, act);
     compact<KMAX>(S.buf, C, k, lane);
-    // one lane per query: after the compaction the buffer holds at most KMAX
-    // entries, the k best among them; one descending sorting network puts them,
-    // smallest last, in the last k slots (pads of kKeyInf in front), and the row
-    // is written straight from the network's registers
-    if (G == 1) {
-      unsigned long long v[KMAX];
+    // after the compaction a lane's buffer holds at most KMAX entries, the k best
+    // of the lane's sources among them; one descending sorting network puts them,
+    // smallest last, in the last slots (pads of kKeyInf in front)
+    unsigned long long v[KMAX];
 #pragma unroll
-      for (int i = 0; i < KMAX; ++i) {
-        const uint2 e = S.buf[i][lane];
-        v[i] = i < C.nb ? (((unsigned long long)e.x << 32) | (e.y + 1u)) : kKeyInf;
-      }
-      sort_desc<KMAX>(v);
+    for (int i = 0; i < KMAX; ++i) {
+      const uint2 e = S.buf[i][lane];
+      v[i] = i < C.nb ? (((unsigned long long)e.x << 32) | (e.y + 1u)) : kKeyInf;
+    }
+    sort_desc<KMAX>(v);
+    if (G == 1) {  // one lane per query: the row is written straight from the network's registers
       if (act && !broken) {
         const int64_t row = order == 0 ? (int64_t)__float_as_int(qp.w) : (int64_t)(qfirst + qi);
         int32_t* oi = out_idx + row * k_row + col0;
@@ -1095,17 +1074,15 @@ __device__ __forceinline__ void l2l_leaf(const L2LArgs& A, int64_t leaf, int64_t
         }
       }
     } else {
+      // G lanes per query: each sub-lane's list (ascending, kKeyInf pads last) is
+      // merged with its partners' (butterfly), keeping the KMAX smallest keys
       RegTopK<unsigned long long, KMAX> T;
-      select_exact<KMAX>(S.buf, C.nb, k, lane, T);
-      __syncwarp();
-      // merge the G partial lists of each query (butterfly over the sub-lanes)
+#pragma unroll
+      for (int e = 0; e < KMAX; ++e) T.t[e] = v[KMAX - 1 - e];
       for (int st = 1; st < G; st <<= 1) {
         unsigned long long pb[KMAX];
 #pragma unroll
         for (int e = 0; e < KMAX; ++e) pb[e] = __shfl_xor_sync(kFull, T.t[e], st);
-        // the partner's pads (0) are not candidates: lift them out of the way
-#pragma unroll
-        for (int e = 0; e < KMAX; ++e) pb[e] = pb[e] == 0ull ? kKeyInf : pb[e];
         T.template merge<KMAX>(pb);
       }
       if (act && sub == 0 && !broken) {
@@ -1114,9 +1091,9 @@ __device__ __forceinline__ void l2l_leaf(const L2LArgs& A, int64_t leaf, int64_t
         float* od = out_d2 + row * k_row + col0;
 #pragma unroll
         for (int e = 0; e < KMAX; ++e) {
-          if (e >= KMAX - k) {
-            oi[e - (KMAX - k)] = (int32_t)(uint32_t)(T.t[e] & 0xffffffffull) - 1;
-            od[e - (KMAX - k)] = __uint_as_float((uint32_t)(T.t[e] >> 32));
+          if (e < k) {
+            oi[e] = (int32_t)(uint32_t)(T.t[e] & 0xffffffffull) - 1;
+            od[e] = __uint_as_float((uint32_t)(T.t[e] >> 32));
           }
         }
       }

@@ -93,3 +93,27 @@ def test_product_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in src.lower().replace("oracle-free", ""), f
+
+
+def test_batch_queue_scratch_and_job_checks():
+    """jzt_batch_queue_bytes is host arithmetic; jzt_batch_run_queue and
+    jzt_batch_run refuse bad jobs before any CUDA work (per-job leaf capacity
+    out of range, missing scratch)."""
+    jzt = _lib()
+    sz = [ctypes.c_size_t(0) for _ in range(3)]
+    for n, b in zip((0, 10, 1000), sz):
+        assert jzt.lib.jzt_batch_queue_bytes(n, ctypes.byref(b)) == 0
+    assert 0 < sz[0].value < sz[1].value < sz[2].value
+    assert sz[2].value % 256 == 0
+    assert jzt.lib.jzt_batch_queue_bytes(-1, ctypes.byref(sz[0])) == jzt.JZT_ERR_INVALID
+    jobs = (jzt.Job * 1)()
+    J = jobs[0]
+    J.d_xyz, J.n, J.op, J.k, J.lane, J.nmax0 = 0x1000, 100, jzt.JZT_OP_KNN, 8, 0, 33
+    J.d_idx, J.d_dist2 = 0x2000, 0x3000
+    ws = (ctypes.c_void_p * 1)(0x100000)
+    wsb = (ctypes.c_size_t * 1)(1 << 30)
+    streams = (ctypes.c_void_p * 1)(None)
+    rc = jzt.lib.jzt_batch_run(jobs, 1, None, ws, wsb, streams, 1, None, ctypes.c_void_p(0x4000))
+    assert rc == jzt.JZT_ERR_INVALID and b"nmax0" in jzt.lib.jzt_last_error()
+    rc = jzt.lib.jzt_batch_run_queue(jobs, 1, None, ws, wsb, streams, 1, None, None, 0, ctypes.c_void_p(0x4000))
+    assert rc == jzt.JZT_ERR_WORKSPACE
