@@ -34,9 +34,9 @@ FP32_LANES_PER_SM = 128
 SMS = 152
 SORT_BYTES_PER_PT = 24    # one LSD pass: read key+value, write key+value (8+4 each way)
 BUILD_FLOOR_BYTES = 42    # read xyz 12 + sorted float4 16 + keys/perm 12 + tree ~2
-# DRAM bytes per point of one k_l2l_knn launch (k = 16): 693 MB read + 2098 MB written
+# DRAM bytes per point of one k_l2l_knn launch (k = 16): 694 MB read + 2097 MB written
 # on 2^24 points, from the ncu capture of this kernel version
-L2L_TRAFFIC_BYTES_PER_PT = (692.6e6 + 2098.0e6) / (1 << 24)
+L2L_TRAFFIC_BYTES_PER_PT = (693.5e6 + 2097.4e6) / (1 << 24)
 
 
 def parse():
