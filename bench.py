@@ -33,6 +33,9 @@ FLOPS_PER_PAIR = 8        # dx, dy, dz, dx*dx, 2 fma (fma = 2 flops)
 FP32_LANES_PER_SM = 128
 SMS = 152
 SORT_BYTES_PER_PT = 24    # one LSD pass: read key+value, write key+value (8+4 each way)
+# bucket sort: scatter reads the key (8) and writes key+index (12); the bin sort reads
+# key+index (12) and the point (12) and writes the key (8) and the float4 point (16)
+BUCKET_SORT_BYTES_PER_PT = 68
 BUILD_FLOOR_BYTES = 42    # read xyz 12 + sorted float4 16 + keys/perm 12 + tree ~2
 # DRAM bytes per point of one k_l2l_knn launch (k = 16): 694 MB read + 2097 MB written
 # on 2^24 points, from the ncu capture of this kernel version
@@ -692,13 +695,17 @@ def main():
                 "work": f"{pairs_per_launch} point pairs x {FLOPS_PER_PAIR} flops per launch",
                 "ms_per_launch": l2l_ms}
     sort_ms = phase_ms.get("sort", 0.0) / max(1, phase_cnt.get("sort", 0))
-    sort_launch_ms = sort_ms / 8.0
-    sort_gbs = SORT_BYTES_PER_PT * n / (sort_launch_ms / 1000.0) / 1e9 if sort_ms else 0.0
+    bucket = st.get("sort_path", 0) == 1
+    sort_launch_ms = sort_ms if bucket else sort_ms / 8.0
+    sort_bytes = BUCKET_SORT_BYTES_PER_PT if bucket else SORT_BYTES_PER_PT
+    sort_gbs = sort_bytes * n / (sort_launch_ms / 1000.0) / 1e9 if sort_ms else 0.0
     build_ms = sum(per.get(ph, 0.0) for ph in ("box", "keys", "sort", "gather", "splits", "nodes"))
     build_floor_gbs = BUILD_FLOOR_BYTES * n / (build_ms / 1000.0) / 1e9 if build_ms else 0.0
-    roof_sort = {"kernel": "k_onesweep", "bound": "hbm", "achieved": sort_gbs, "peak": hbm_peak,
-                 "unit": "GB/s", "frac": sort_gbs / hbm_peak, "traffic": None,
-                 "peak_source": hbm_src, "work": f"{SORT_BYTES_PER_PT} B/pt x {n} per pass",
+    roof_sort = {"kernel": "k_bucket_scatter + k_bin_sort" if bucket else "k_onesweep", "bound": "hbm",
+                 "achieved": sort_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": sort_gbs / hbm_peak,
+                 "traffic": None, "peak_source": hbm_src,
+                 "work": (f"{BUCKET_SORT_BYTES_PER_PT} B/pt x {n} (scatter into fine bins + per-bin sort)" if bucket
+                          else f"{SORT_BYTES_PER_PT} B/pt x {n} per pass"),
                  "ms_per_launch": sort_launch_ms}
     roof_build = {"stage": "build (box, keys, sort, gather, splits, nodes)", "bound": "hbm",
                   "achieved": build_floor_gbs, "peak": hbm_peak, "unit": "GB/s",

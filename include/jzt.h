@@ -68,7 +68,13 @@ typedef struct jzt_params {
                                  comparator; Eq. lvl at float32 precision), for data whose scales
                                  span many orders of magnitude -- results do not change, only the
                                  tree; needs 16 more workspace bytes per point; not with reg_fmax */
-    int32_t reserved[5];      /* must be zero */
+    int32_t lsd_sort;         /* sort of the integer keys (Sec. II-B; the result is the same stable
+                                 order either way): 0 (default) = for N >= 2^16 one scatter of the
+                                 keys into fine bins (their top bits) and one shared-memory sort
+                                 per group of consecutive bins, taken when no fine bin holds more
+                                 than 2048 points and replaced on the device by the LSD radix
+                                 passes otherwise; 1 = always the LSD radix passes */
+    int32_t reserved[4];      /* must be zero */
 } jzt_params;
 
 typedef struct jzt_tree jzt_tree;  /* opaque; lives on the host, points into the workspace */
@@ -81,7 +87,8 @@ typedef struct jzt_status_info {
                                  (a lower bound: later stages may need more) */
     int64_t ilist_entries;    /* interaction-list entries used by the last walk */
     int32_t n_planes;         /* tree-planes built (Sec. II-C) */
-    int32_t reserved;
+    int32_t sort_path;        /* the last build's key sort: 1 = fine-bin bucket sort, 0 = LSD
+                                 radix passes (or the float z-order's merge sort) */
     int64_t n_nodes[16];      /* nodes per plane, plane 0 = leaves; [n_planes] = super nodes */
     int64_t knn_pairs;        /* point pairs evaluated by the last kNN LeafToLeaf */
     int64_t fof_pairs;        /* point pairs evaluated by the last FoF LeafToLeaf */

@@ -60,7 +60,7 @@ class Params(ctypes.Structure):
                 ("n_target", ctypes.c_int32), ("ngr", ctypes.c_int32),
                 ("alloc_fac_nodes", ctypes.c_float), ("alloc_fac_ilist", ctypes.c_float),
                 ("heap_size", ctypes.c_int32), ("reg_fmax", ctypes.c_float), ("float_order", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("lsd_sort", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class Job(ctypes.Structure):
@@ -74,7 +74,7 @@ class Job(ctypes.Structure):
 class StatusInfo(ctypes.Structure):
     _fields_ = [("code", ctypes.c_int32), ("detail", ctypes.c_int32),
                 ("required_bytes", ctypes.c_int64), ("ilist_entries", ctypes.c_int64),
-                ("n_planes", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_planes", ctypes.c_int32), ("sort_path", ctypes.c_int32),
                 ("n_nodes", ctypes.c_int64 * 16), ("knn_pairs", ctypes.c_int64),
                 ("fof_pairs", ctypes.c_int64), ("knn_stats", ctypes.c_int64 * 8),
                 ("knn_plane_entries", ctypes.c_int64 * 16)]
@@ -185,7 +185,7 @@ def status(workspace: torch.Tensor, stream=None, raise_on_error: bool = False) -
         _check(rc)
     out = dict(code=info.code, name=_NAMES.get(info.code, str(info.code)), detail=info.detail,
                required_bytes=info.required_bytes, ilist_entries=info.ilist_entries,
-               n_planes=info.n_planes, n_nodes=[info.n_nodes[i] for i in range(16)],
+               n_planes=info.n_planes, sort_path=info.sort_path, n_nodes=[info.n_nodes[i] for i in range(16)],
                knn_pairs=info.knn_pairs, fof_pairs=info.fof_pairs,
                knn_stats=[info.knn_stats[i] for i in range(8)],
                knn_plane_entries=[info.knn_plane_entries[i] for i in range(16)])

@@ -36,8 +36,9 @@ int resolve_params(const jzt_params* p, Params* out, const char** why) {
   P.fac_ilist = 128.0f;
   P.reg_fmax = 0.0f;
   P.float_order = 0;
+  P.lsd_sort = 0;
   if (p) {
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
       if (p->reserved[i] != 0) {
         *why = "jzt_params.reserved must be zero";
         return JZT_ERR_INVALID;
@@ -51,6 +52,11 @@ int resolve_params(const jzt_params* p, Params* out, const char** why) {
     if (p->alloc_fac_ilist != 0.0f) P.fac_ilist = p->alloc_fac_ilist;
     P.reg_fmax = p->reg_fmax;
     P.float_order = p->float_order;
+    P.lsd_sort = p->lsd_sort;
+  }
+  if (P.lsd_sort != 0 && P.lsd_sort != 1) {
+    *why = "lsd_sort must be 0 or 1";
+    return JZT_ERR_INVALID;
   }
   if (P.float_order != 0 && P.float_order != 1) {
     *why = "float_order must be 0 or 1";
@@ -103,6 +109,9 @@ int compute_layout(int64_t n, const Params& P, int k, size_t ws_bytes, Layout* L
   L.heap = P.heap;
   L.reg_fmax = P.reg_fmax;
   L.float_order = P.float_order;
+  L.bucket_sort = (!P.float_order && !P.lsd_sort && n >= kBucketMinN) ? 1 : 0;
+  L.fine_bits = 1;  // top F key bits, about 32 points per fine bin on average
+  while (L.fine_bits < kMaxFineBits && (n >> (L.fine_bits + 1)) >= 32) ++L.fine_bits;
   L.n_planes = num_planes(n, P);
   // Node capacity per plane: fac * N / (N_max^(p)/2) (Eq. alloc_nodes).  The
   // estimate is not a bound (Sec. II-C), so the small upper planes get 4x the
@@ -426,6 +435,7 @@ int jzt_status(const void* d_ws, void* stream, jzt_status_info* info) {
     info->required_bytes = m.required_bytes;
     info->ilist_entries = (int64_t)m.arena_peak;
     info->n_planes = m.n_planes;
+    info->sort_path = m.bucket_max <= (uint32_t)kGrpStep ? 1 : 0;
     for (int p = 0; p < 16 && p < kMaxPlanes + 1; ++p) info->n_nodes[p] = m.n_nodes[p];
     info->knn_pairs = (int64_t)m.knn_pairs;
     for (int t = 0; t < 8; ++t) info->knn_stats[t] = (int64_t)m.knn_stats[t];

@@ -1,5 +1,6 @@
-// Tree construction on the device (Sec. II): domain, Morton keys, LSD radix
-// sort, gather, gap levels and tree-plane splits, node records.
+// Tree construction on the device (Sec. II): domain, Morton keys, the key sort
+// (fine-bin bucket sort, or LSD radix passes), gather, gap levels and
+// tree-plane splits, node records.
 //
 // Layout in HBM (all in the caller's workspace):
 //   keys  uint64[N] x2 and vals uint32[N] x2 (radix ping-pong), sorted points
@@ -105,7 +106,7 @@ __device__ unsigned long long chained_scan(unsigned long long* st, int64_t tile,
 
 // ------------------------------------------------------------------ meta / box
 
-__global__ void k_init_meta(Meta* m, int n_planes) {
+__global__ void k_init_meta(Meta* m, int n_planes, int bucket_sort) {
   int t = threadIdx.x;
   if (t == 0) {
     m->status = 0;
@@ -133,6 +134,9 @@ __global__ void k_init_meta(Meta* m, int n_planes) {
   if (t == 0) {
     m->knn_pairs = 0;
     m->fof_pairs = 0;
+    m->bucket_max = bucket_sort ? 0u : 0xffffffffu;  // no bucket sort tried: as if rejected
+    m->big_bins = 0;
+    m->big_next = 0;
   }
   if (t < 32) m->tile_ctr[t] = 0;
   uint32_t* h = &m->radix_hist[0][0];
@@ -140,6 +144,19 @@ __global__ void k_init_meta(Meta* m, int n_planes) {
 }
 
 __global__ void k_zero_u64(unsigned long long* p, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = 0ull;
+}
+
+// The LSD radix passes of a build that tried the bucket sort run only when the
+// device rejected it (a fine bin above kGrpStep keys); `gated` = 0: always.
+__device__ __forceinline__ bool lsd_skipped(const Meta* m, int gated) {
+  return gated && m->bucket_max <= (uint32_t)kGrpStep;
+}
+
+__global__ void k_zero_u64_gated(unsigned long long* p, int64_t n, const Meta* m) {
+  if (lsd_skipped(m, 1)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = 0ull;
@@ -273,11 +290,36 @@ __device__ __forceinline__ void hist_key(uint32_t (*sh)[kRadixBins], uint64_t ke
   }
 }
 
+// Fine-bin counts of a thread's consecutive keys: one atomic per run of equal bins.
+__device__ __forceinline__ void fine_count(uint32_t* __restrict__ fine, const uint64_t (&k4)[4], int cnt,
+                                           int shift) {
+  uint32_t bin = 0, run = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (e < cnt) {
+      const uint32_t b = (uint32_t)(k4[e] >> shift);
+      if (run && b == bin) {
+        ++run;
+      } else {
+        if (run) atomicAdd(&fine[bin], run);
+        bin = b;
+        run = 1;
+      }
+    }
+  }
+  if (run) atomicAdd(&fine[bin], run);
+}
+
+// Keys of all points plus either the digit histograms of the LSD passes
+// (fine == nullptr) or the counts of the 2^F fine bins (key >> fshift).
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_keygen(const float* __restrict__ xyz, int64_t n, Meta* m,
-                                                uint64_t* __restrict__ keys) {
+                                                uint64_t* __restrict__ keys, uint32_t* __restrict__ fine,
+                                                int fshift) {
   __shared__ uint32_t sh[kRadixPasses][kRadixBins];
-  for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) (&sh[0][0])[i] = 0;
+  const bool digits = fine == nullptr;
+  if (digits)
+    for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) (&sh[0][0])[i] = 0;
   __syncthreads();
   const float lo[3] = {m->lo[0], m->lo[1], m->lo[2]};
   const float sc = m->scale;
@@ -304,13 +346,22 @@ __global__ void __launch_bounds__(256) k_keygen(const float* __restrict__ xyz, i
         o[1] = make_ulonglong2(k4[2], k4[3]);
         cnt = 4;
       } else if (g < ng) {
-        for (int64_t i = 4 * g; i < n; ++i, ++cnt) {
-          k4[cnt] = morton(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lo, sc);
-          keys[i] = k4[cnt];
+        cnt = (int)(n - 4 * g);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (e < cnt) {
+            const int64_t i = 4 * g + e;
+            k4[e] = morton(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lo, sc);
+            keys[i] = k4[e];
+          }
         }
       }
+      if (digits) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) hist_key(sh, k4[e], e < cnt);
+        for (int e = 0; e < 4; ++e) hist_key(sh, k4[e], e < cnt);
+      } else {
+        fine_count(fine, k4, cnt, fshift);
+      }
     }
   } else {
     const int64_t rounds = (n + nth - 1) / nth;
@@ -321,9 +372,11 @@ __global__ void __launch_bounds__(256) k_keygen(const float* __restrict__ xyz, i
         k = morton(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lo, sc);
         keys[i] = k;
       }
-      hist_key(sh, k, i < n);
+      if (digits) hist_key(sh, k, i < n);
+      else if (i < n) atomicAdd(&fine[k >> fshift], 1u);
     }
   }
+  if (!digits) return;
   __syncthreads();
   for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) {
     uint32_t v = (&sh[0][0])[i];
@@ -332,9 +385,9 @@ __global__ void __launch_bounds__(256) k_keygen(const float* __restrict__ xyz, i
 }
 
 // Exclusive digit offsets of `passes` passes of `bins` digits (one warp per pass).
-__global__ void k_radix_offsets(Meta* m, int passes, int bins) {
+__global__ void k_radix_offsets(Meta* m, int passes, int bins, int gated) {
   const int p = warp_id();
-  if (p >= passes) return;
+  if (p >= passes || lsd_skipped(m, gated)) return;
   uint32_t run = 0;
   for (int b0 = 0; b0 < bins; b0 += 32) {
     uint32_t v = m->radix_hist[p][b0 + lane_id()];
@@ -427,7 +480,9 @@ template <int BITS, bool GATHER>
 __global__ void __launch_bounds__(kSortThreads, 3)
     k_onesweep(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
                uint32_t* __restrict__ vout, int64_t n, int pass, int shift, uint32_t* lookback, Meta* m,
-               const float* __restrict__ xa, const float* __restrict__ xb, int64_t na, float4* __restrict__ pts) {
+               const float* __restrict__ xa, const float* __restrict__ xb, int64_t na, float4* __restrict__ pts,
+               int gated) {
+  if (lsd_skipped(m, gated)) return;
   constexpr int kBins = 1 << BITS;
   constexpr int DPT = kBins / kSortThreads;  // digits per thread
   constexpr int W = kSortThreads / 32;
@@ -545,6 +600,443 @@ __global__ void __launch_bounds__(kSortThreads, 3)
         vout[g] = v;
       }
     }
+  }
+}
+
+// ---------------------------------------------------------------- bucket sort
+//
+// The same stable order of the integer keys (ties by original index) in fewer
+// sweeps over memory and far fewer instructions per key, for sets whose fine
+// bins (the top F key bits, about 32-64 keys each on average) each hold at most
+// kGrpStep keys -- every nearly uniform set, the Zel'dovich lattices included:
+//  1. k_keygen counts the keys per fine bin;
+//  2. k_fine_scan turns the counts into each bin's first position (chained scan)
+//     and records the largest count, which decides the path on the device;
+//  3. k_bucket_scatter moves every (key, index) to its bin (order within a bin
+//     arbitrary: one atomic per run of a warp's consecutive keys that share a bin);
+//  4. k_bin_sort sorts each bin of at most kBinWarpMax keys by one warp, in
+//     registers, with a bitonic network on (key, index) -- which also restores
+//     the input order among equal keys -- and writes the sorted keys and the
+//     sorted points float4(x, y, z, original index); larger bins are listed;
+//  5. k_big_bins sorts the listed bins in shared memory by stable counting
+//     passes over the bits that vary within the bin (index passes first where
+//     equal keys occur).
+// When a bin holds more than kGrpStep keys, steps 3-5 return at once and the
+// LSD radix passes (launched gated) sort the keys of step 1 instead.
+static_assert(kRadixPasses % 2 == 0, "the keys of an even number of LSD passes start in keys_a");
+constexpr int kBinWarpMax = 128;   // bins up to this size: one warp, keys in registers
+constexpr int kScatterRounds = 8;  // rounds of 32 keys per warp and chunk of the scatter
+
+// Exclusive prefix of the fine-bin counts in place (fine) and as the scatter
+// cursors (cur); tiles of kFineScanTile bins claimed in order, chained scan.
+__global__ void __launch_bounds__(256) k_fine_scan(uint32_t* __restrict__ fine, uint32_t* __restrict__ cur,
+                                                   int64_t nb, unsigned long long* st, Meta* m) {
+  __shared__ int64_t s_tile;
+  __shared__ unsigned long long s_pre;
+  __shared__ uint32_t s_max;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    s_tile = atomicAdd(&m->tile_ctr[kCtrFine], 1u);
+    s_max = 0;
+  }
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t base = tile * kFineScanTile + (int64_t)t * 16;  // nb is a multiple of 16
+  uint32_t v[16];
+  uint32_t sum = 0, mx = 0;
+  if (base < nb) {
+    const uint4* p4 = reinterpret_cast<const uint4*>(fine + base);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 u = p4[q];
+      v[4 * q] = u.x;
+      v[4 * q + 1] = u.y;
+      v[4 * q + 2] = u.z;
+      v[4 * q + 3] = u.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = 0;
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    sum += v[i];
+    mx = max(mx, v[i]);
+  }
+  if (mx) atomicMax(&s_max, mx);
+  uint32_t total;
+  const uint32_t ex = block_excl_scan<256>(sum, &total);
+  if (warp_id() == 0) {
+    const unsigned long long pre = chained_scan(st, tile, total, m, kStageSort);
+    if (lane_id() == 0) s_pre = pre;
+  }
+  __syncthreads();
+  if (t == 0 && s_max) atomicMax(&m->bucket_max, s_max);
+  if (base >= nb) return;
+  uint32_t run = (uint32_t)s_pre + ex;
+  uint4* f4 = reinterpret_cast<uint4*>(fine + base);
+  uint4* c4 = reinterpret_cast<uint4*>(cur + base);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint4 o;
+    o.x = run;
+    run += v[4 * q];
+    o.y = run;
+    run += v[4 * q + 1];
+    o.z = run;
+    run += v[4 * q + 2];
+    o.w = run;
+    run += v[4 * q + 3];
+    f4[q] = o;
+    c4[q] = o;
+  }
+}
+
+// Every key (and its index) to the next free slot of its fine bin.  A warp takes
+// 32 kScatterRounds consecutive keys, 32 per round (lane l: key 32 r + l); the
+// lanes of a run of equal bins within a round take consecutive slots from one
+// atomic of the run's first lane, so that they write consecutive addresses.  The
+// atomics of all rounds are issued before any store.
+__global__ void __launch_bounds__(256) k_bucket_scatter(const uint64_t* __restrict__ keys, int64_t n, int fshift,
+                                                        uint32_t* __restrict__ cur, uint64_t* __restrict__ kb,
+                                                        uint32_t* __restrict__ vb, const Meta* m) {
+  if (m->bucket_max > (uint32_t)kGrpStep) return;
+  constexpr int R = kScatterRounds;
+  const int lane = lane_id();
+  const unsigned upto = (2u << lane) - 1u;  // lanes <= lane (all ones for lane 31)
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t n_chunks = (n + 32 * R - 1) / (32 * R);
+  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += nw) {
+    const int64_t base = c * 32 * R;
+    uint64_t k[R];
+    uint32_t bn[R], pos[R];
+    unsigned starts[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t j = base + 32 * r + lane;
+      k[r] = j < n ? keys[j] : 0ull;
+      bn[r] = j < n ? (uint32_t)(k[r] >> fshift) : 0xffffffffu;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const bool valid = base + 32 * r + lane < n;  // the valid lanes are a prefix
+      const uint32_t prev = __shfl_up_sync(0xffffffffu, bn[r], 1);
+      const bool start = valid && (lane == 0 || prev != bn[r]);
+      starts[r] = __ballot_sync(0xffffffffu, start);
+      const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+      const unsigned after = starts[r] & ~upto;
+      const int end = after ? __ffs(after) - 1 : __popc(vmask);
+      pos[r] = start ? atomicAdd(&cur[bn[r]], (uint32_t)(end - lane)) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t j = base + 32 * r + lane;
+      const int leader = 31 - __clz(starts[r] & upto);
+      const uint32_t p = __shfl_sync(0xffffffffu, pos[r], leader < 0 ? 0 : leader) + (uint32_t)(lane - leader);
+      if (j < n && p < (uint64_t)n) {  // always in range: the counts came from the same keys
+        kb[p] = k[r];
+        vb[p] = (uint32_t)j;
+      }
+    }
+  }
+}
+
+// Sorted key and point at sorted position g.
+__device__ __forceinline__ void put_sorted(int64_t g, uint64_t key, uint32_t p0, int64_t n, uint64_t* __restrict__ kout,
+                                           const float* __restrict__ xa, const float* __restrict__ xb, int64_t na,
+                                           float4* __restrict__ pts) {
+  kout[g] = key;
+  const uint32_t p = p0 < (uint64_t)n ? p0 : 0u;
+  const float* sp = (int64_t)p < na ? xa + 3 * (int64_t)p : xb + 3 * ((int64_t)p - na);
+  pts[g] = make_float4(__ldg(sp), __ldg(sp + 1), __ldg(sp + 2), __uint_as_float(p));
+}
+
+// Bitonic network over the 32 E elements of a warp (element i = 32 e + lane in
+// register e of the lane), ascending by key and, with FULL, by index among equal
+// keys.
+template <int E, bool FULL>
+__device__ __forceinline__ void warp_bitonic(uint64_t (&k)[E], uint32_t (&v)[E]) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int size = 2; size <= 32 * E; size <<= 1) {
+#pragma unroll
+    for (int st = size >> 1; st > 0; st >>= 1) {
+      if (st >= 32) {
+        const int es = st / 32;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if ((e & es) == 0) {
+            const int f = e | es;
+            const bool up = ((32 * e + lane) & size) == 0;
+            const bool gt = k[e] > k[f] || (FULL && k[e] == k[f] && v[e] > v[f]);
+            if (gt == up) {
+              const uint64_t tk = k[e];
+              k[e] = k[f];
+              k[f] = tk;
+              const uint32_t tv = v[e];
+              v[e] = v[f];
+              v[f] = tv;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const uint64_t ok = __shfl_xor_sync(0xffffffffu, k[e], st);
+          const uint32_t ov = __shfl_xor_sync(0xffffffffu, v[e], st);
+          const bool up = ((32 * e + lane) & size) == 0;
+          const bool lower = (lane & st) == 0;
+          // the lower slot of an ascending pair keeps the smaller; strict tests on both
+          // sides, so that equal keys (compared without the index) stay where they are
+          const bool other_less = ok < k[e] || (FULL && ok == k[e] && ov < v[e]);
+          const bool other_more = ok > k[e] || (FULL && ok == k[e] && ov > v[e]);
+          if ((lower == up) ? other_less : other_more) {
+            k[e] = ok;
+            v[e] = ov;
+          }
+        }
+      }
+    }
+  }
+}
+
+// One bin of cnt <= 32 E keys sorted by one warp in registers (pads: all ones,
+// after every key of 63 bits).  The network compares keys only; where equal keys
+// end up adjacent it runs again comparing (key, index), which puts them in input
+// order.
+template <int E>
+__device__ __forceinline__ void bin_sort_warp(const uint64_t* __restrict__ kb, const uint32_t* __restrict__ vb,
+                                              int64_t e0, int cnt, int64_t n, uint64_t* __restrict__ kout,
+                                              const float* __restrict__ xa, const float* __restrict__ xb, int64_t na,
+                                              float4* __restrict__ pts) {
+  const int lane = lane_id();
+  uint64_t k[E];
+  uint32_t v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = 32 * e + lane;
+    k[e] = i < cnt ? kb[e0 + i] : ~0ull;
+    v[e] = i < cnt ? vb[e0 + i] : ~0u;
+  }
+  warp_bitonic<E, false>(k, v);
+  bool tie = false;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {  // element i + 1: the next lane, or lane 0 of the next register
+    const uint64_t dn = __shfl_down_sync(0xffffffffu, k[e], 1);
+    const uint64_t wrap = __shfl_sync(0xffffffffu, k[e + 1 < E ? e + 1 : e], 0);
+    const uint64_t nx = lane < 31 ? dn : wrap;
+    const int i = 32 * e + lane;
+    tie = tie || (i + 1 < cnt && nx == k[e]);
+  }
+  if (__any_sync(0xffffffffu, tie)) warp_bitonic<E, true>(k, v);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = 32 * e + lane;
+    if (i < cnt) put_sorted(e0 + i, k[e], v[e], n, kout, xa, xb, na, pts);
+  }
+}
+
+// Warps take chunks of 32 consecutive bins; bins above kBinWarpMax keys go to
+// the list `big` (count in Meta::big_bins) for k_big_bins.
+__global__ void __launch_bounds__(256) k_bin_sort(const uint64_t* __restrict__ kb, const uint32_t* __restrict__ vb,
+                                                  const uint32_t* __restrict__ off, int64_t nb, int64_t n,
+                                                  uint64_t* __restrict__ kout, const float* __restrict__ xa,
+                                                  const float* __restrict__ xb, int64_t na, float4* __restrict__ pts,
+                                                  uint32_t* __restrict__ big, Meta* m) {
+  if (m->bucket_max > (uint32_t)kGrpStep) return;
+  const int lane = lane_id();
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t n_chunks = (nb + 31) / 32;
+  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += nw) {
+    const int64_t b = 32 * c + lane;
+    const int64_t lo = b < nb ? (int64_t)off[b] : n;
+    const int64_t hi = b + 1 < nb ? (int64_t)off[b + 1] : n;
+    const int my_cnt = (int)(hi - lo);
+    unsigned todo = __ballot_sync(0xffffffffu, my_cnt > 0);
+    while (todo) {
+      const int j = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int64_t e0 = __shfl_sync(0xffffffffu, lo, j);
+      const int cnt = __shfl_sync(0xffffffffu, my_cnt, j);
+      if (cnt <= 32) {
+        bin_sort_warp<1>(kb, vb, e0, cnt, n, kout, xa, xb, na, pts);
+      } else if (cnt <= 64) {
+        bin_sort_warp<2>(kb, vb, e0, cnt, n, kout, xa, xb, na, pts);
+      } else if (cnt <= kBinWarpMax) {
+        bin_sort_warp<4>(kb, vb, e0, cnt, n, kout, xa, xb, na, pts);
+      } else if (lane == 0) {
+        big[atomicAdd(&m->big_bins, 1u)] = (uint32_t)(32 * c + j);
+      }
+    }
+  }
+}
+
+struct GrpSmem {
+  uint64_t k[2][kGrpCap];  // keys (ping-pong)
+  uint32_t v[2][kGrpCap];  // original indices
+  uint16_t whist[kGrpThreads / 32][256];
+  uint32_t dstart[256];
+  unsigned long long kx;   // OR over the bin of key ^ first key: the varying bits
+  uint32_t vx;             // the same for the indices
+  uint32_t item;
+};
+
+// One stable counting pass of the cnt elements of buffer src into src ^ 1 by the
+// 8-bit digit at bit sh of the key (IDX: of the index).  Warp w ranks elements
+// [w, w + 1) * 32 ipt, round i the 32 elements from 32 (w ipt + i): the order of
+// (warp, round, lane) is the element order, so the pass is stable.
+template <bool IDX>
+__device__ __forceinline__ void grp_pass(GrpSmem& S, int src, int cnt, int ipt, int sh) {
+  const int t = threadIdx.x, w = warp_id(), lane = lane_id();
+  for (int i = t; i < (kGrpThreads / 32) * 256; i += kGrpThreads) (&S.whist[0][0])[i] = 0;
+  __syncthreads();
+  const unsigned lt = lanemask_lt();
+  const int lofs = w * ipt * 32 + lane;
+  uint32_t dig[kGrpIpt], rank[kGrpIpt];
+#pragma unroll
+  for (int i = 0; i < kGrpIpt; ++i) {
+    dig[i] = 0;
+    rank[i] = 0;
+    if (i < ipt) {
+      const int e = lofs + 32 * i;
+      const bool valid = e < cnt;
+      uint32_t d = 0;
+      if (valid) d = IDX ? (S.v[src][e] >> sh) & 255u : (uint32_t)(S.k[src][e] >> sh) & 255u;
+      unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? bb : ~bb;
+      }
+      const int leader = valid ? __ffs(peers) - 1 : lane;
+      uint32_t old = 0;
+      if (valid && lane == leader) {
+        old = S.whist[w][d];
+        S.whist[w][d] = (uint16_t)(old + __popc(peers));
+      }
+      old = __shfl_sync(0xffffffffu, old, leader);
+      dig[i] = d;
+      rank[i] = old + __popc(peers & lt);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // digit t: each warp's offset within the digit, then the digit's start
+  uint32_t run = 0;
+#pragma unroll
+  for (int ww = 0; ww < kGrpThreads / 32; ++ww) {
+    const uint32_t c = S.whist[ww][t];
+    S.whist[ww][t] = (uint16_t)run;
+    run += c;
+  }
+  uint32_t total;
+  S.dstart[t] = block_excl_scan<kGrpThreads>(run, &total);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kGrpIpt; ++i) {
+    const int e = lofs + 32 * i;
+    if (i < ipt && e < cnt) {
+      const uint32_t pos = S.dstart[dig[i]] + S.whist[w][dig[i]] + rank[i];
+      S.k[src ^ 1][pos] = S.k[src][e];
+      S.v[src ^ 1][pos] = S.v[src][e];
+    }
+  }
+  __syncthreads();
+}
+
+// The listed bins (more than kBinWarpMax keys, at most kGrpStep <= kGrpCap),
+// one at a time per block, taken from a shared counter.
+__global__ void __launch_bounds__(kGrpThreads, 2)
+    k_big_bins(const uint64_t* __restrict__ kb, const uint32_t* __restrict__ vb, const uint32_t* __restrict__ off,
+               const uint32_t* __restrict__ big, int64_t nb, int64_t n, uint64_t* __restrict__ kout,
+               const float* __restrict__ xa, const float* __restrict__ xb, int64_t na, float4* __restrict__ pts,
+               Meta* m) {
+  if (m->bucket_max > (uint32_t)kGrpStep) return;
+  extern __shared__ __align__(16) unsigned char grp_smem[];
+  GrpSmem& S = *reinterpret_cast<GrpSmem*>(grp_smem);
+  const int t = threadIdx.x;
+  const uint32_t n_big = m->big_bins;
+  while (true) {
+    if (t == 0) {
+      S.item = atomicAdd(&m->big_next, 1u);
+      S.kx = 0;
+      S.vx = 0;
+    }
+    __syncthreads();
+    const uint32_t item = S.item;
+    if (item >= n_big) return;
+    const int64_t b = big[item];
+    const int64_t e0 = off[b];
+    const int cnt = (int)((b + 1 < nb ? (int64_t)off[b + 1] : n) - e0);
+    if (cnt > kGrpCap) {  // cannot happen while every bin holds at most kGrpStep keys
+      if (t == 0) set_error(m, JZT_ERR_INTERNAL, kStageSort);
+      return;
+    }
+    const uint64_t kf = kb[e0];
+    const uint32_t vf = vb[e0];
+    unsigned long long kx = 0;
+    uint32_t vx = 0;
+    for (int j = t; j < cnt; j += kGrpThreads) {
+      const uint64_t k = kb[e0 + j];
+      const uint32_t v = vb[e0 + j];
+      S.k[0][j] = k;
+      S.v[0][j] = v;
+      kx |= k ^ kf;
+      vx |= v ^ vf;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      kx |= __shfl_xor_sync(0xffffffffu, kx, o);
+      vx |= __shfl_xor_sync(0xffffffffu, vx, o);
+    }
+    if (lane_id() == 0) {
+      if (kx) atomicOr(&S.kx, kx);
+      if (vx) atomicOr(&S.vx, vx);
+    }
+    __syncthreads();
+    const int hb = S.kx ? 64 - __clzll((long long)S.kx) : 0;
+    const int ipt = (cnt + kGrpThreads - 1) / kGrpThreads;
+    int src = 0;
+    for (int sh = 0; sh < hb; sh += 8) {
+      grp_pass<false>(S, src, cnt, ipt, sh);
+      src ^= 1;
+    }
+    // equal keys are now adjacent but in the arbitrary order of the scatter: if
+    // there are any, the passes run again over the index first
+    bool eq = false;
+    for (int j = t; j + 1 < cnt; j += kGrpThreads) eq = eq || S.k[src][j] == S.k[src][j + 1];
+    if (__syncthreads_or(eq)) {
+      const int hbv = S.vx ? 32 - __clz((int)S.vx) : 0;
+      for (int sh = 0; sh < hbv; sh += 8) {
+        grp_pass<true>(S, src, cnt, ipt, sh);
+        src ^= 1;
+      }
+      for (int sh = 0; sh < hb; sh += 8) {
+        grp_pass<false>(S, src, cnt, ipt, sh);
+        src ^= 1;
+      }
+    }
+    for (int j = t; j < cnt; j += kGrpThreads) put_sorted(e0 + j, S.k[src][j], S.v[src][j], n, kout, xa, xb, na, pts);
+    __syncthreads();  // the buffers and S.item are reused by the next bin
+  }
+}
+
+// Digit histograms of the LSD passes from the keys (bucket sort rejected).
+__global__ void __launch_bounds__(256) k_lsd_hist(const uint64_t* __restrict__ keys, int64_t n, Meta* m) {
+  if (lsd_skipped(m, 1)) return;
+  __shared__ uint32_t sh[kRadixPasses][kRadixBins];
+  for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int64_t rounds = (n + nth - 1) / nth;
+  for (int64_t r = 0; r < rounds; ++r) {
+    const int64_t i = r * nth + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    hist_key(sh, i < n ? keys[i] : 0ull, i < n);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) {
+    const uint32_t v = (&sh[0][0])[i];
+    if (v) atomicAdd(&m->radix_hist[i / kRadixBins][i % kRadixBins], v);
   }
 }
 
@@ -674,7 +1166,6 @@ __device__ __forceinline__ int level_ext(uint64_t ka, uint64_t kb, int64_t a, in
 // search of Sec. II-C, step 2).  Gaps 0 and N are always splits.  The flags
 // are compacted in one pass (chained scan) into spl0 = split gap indices.
 constexpr int kSplitThreads = 256;
-constexpr int kSplitPer = kScanTile / kSplitThreads;  // gaps per thread
 
 // The two sources of levels: integer Morton keys (levels -32..64 fit in int8)
 // and the float z-order of the sorted points themselves (levels -479..388).
@@ -682,6 +1173,7 @@ struct KeyLevels {
   using Elem = uint64_t;
   using Lvl = int8_t;
   static constexpr int kNone = 127;
+  static constexpr int kTile = 2048;  // gaps per tile (large tiles: few chained-scan steps)
   __device__ static Elem load(const void* src, int64_t pos) { return static_cast<const uint64_t*>(src)[pos]; }
   __device__ static Elem pad() { return 0ull; }
   __device__ static int level(const Elem& a, const Elem& b, int64_t ia, int64_t ib) { return level_ext(a, b, ia, ib); }
@@ -690,6 +1182,7 @@ struct FloatLevels {
   using Elem = float4;
   using Lvl = int16_t;
   static constexpr int kNone = kZNoLevel;
+  static constexpr int kTile = 2048;  // 16-byte elements: the tile's points fit 48 KB of shared memory
   __device__ static Elem load(const void* src, int64_t pos) { return static_cast<const float4*>(src)[pos]; }
   __device__ static Elem pad() { return make_float4(0.f, 0.f, 0.f, 0.f); }
   __device__ static int level(const Elem& a, const Elem& b, int64_t ia, int64_t ib) { return zlevel(a, b, ia, ib); }
@@ -702,48 +1195,51 @@ __global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const void* __res
                                                                Meta* m) {
   using Elem = typename Src::Elem;
   using Lvl = typename Src::Lvl;
-  __shared__ Elem s_key[kScanTile + 2 * 32 + 1];
-  __shared__ Lvl s_w[kScanTile + 32];
-  __shared__ Lvl s_pre[kScanTile + 32], s_suf[kScanTile + 32];
+  constexpr int kLeafTile = Src::kTile;
+  constexpr int kSplitPer = kLeafTile / kSplitThreads;  // gaps per thread
+  __shared__ Elem s_key[kLeafTile + 2 * 32 + 1];
+  __shared__ Lvl s_w[kLeafTile + 32];
+  __shared__ Lvl s_pre[kLeafTile + 32];
   __shared__ uint32_t s_tile;
   const int reg_lvl = m->reg_lvl[0];
   if (threadIdx.x == 0) s_tile = atomicAdd(&m->tile_ctr[kCtrLeafSplits], 1u);
   __syncthreads();
   const int64_t tile = s_tile;
-  const int64_t g0 = tile * kScanTile;
+  const int64_t g0 = tile * kLeafTile;
   // keys at positions [g0 - M, g0 + T + M)
   const int64_t k0 = g0 - M;
-  const int nk = kScanTile + 2 * M;
+  const int nk = kLeafTile + 2 * M;
   for (int t = threadIdx.x; t < nk; t += kSplitThreads) {
     int64_t pos = k0 + t;
     s_key[t] = (pos >= 0 && pos < n) ? Src::load(src, pos) : Src::pad();
   }
   __syncthreads();
   // window levels w_j = level(j, j+M) for j in [g0 - M, g0 + T)
-  for (int t = threadIdx.x; t < kScanTile + M; t += kSplitThreads) {
+  for (int t = threadIdx.x; t < kLeafTile + M; t += kSplitThreads) {
     int64_t j = k0 + t;
     int v = Src::kNone;
     if (j >= 0 && j + M < n) v = Src::level(s_key[t], s_key[t + M], j, j + M);
     s_w[t] = (Lvl)v;
   }
   __syncthreads();
-  // sliding minimum of width M over s_w: per block of M slots (aligned at 0),
-  // prefix and suffix minima; the window [u, u + M - 1] meets at most two blocks
-  const int nw = kScanTile + M;
-  for (int b0 = threadIdx.x * M; b0 < nw; b0 += kSplitThreads * M) {
-    const int b1 = min(b0 + M, nw);
-    int run = Src::kNone;
-    for (int t = b0; t < b1; ++t) {
-      run = min(run, (int)s_w[t]);
-      s_pre[t] = (Lvl)run;
-    }
-    run = Src::kNone;
-    for (int t = b1 - 1; t >= b0; --t) {
-      run = min(run, (int)s_w[t]);
-      s_suf[t] = (Lvl)run;
-    }
+  // sliding minimum of width M over s_w by doubling: after step j, slot u holds the
+  // minimum of s_w[u .. u + 2^(j+1) - 1]; with 2^kd <= M < 2^(kd+1) the window
+  // [u, u + M - 1] is the union of the ranges of length 2^kd at u and u + M - 2^kd
+  const int nw = kLeafTile + M;
+  int kd = 0;
+  while ((2 << kd) <= M) ++kd;
+  Lvl* cur_t = s_w;
+  Lvl* nxt_t = s_pre;
+  for (int j = 0; j < kd; ++j) {
+    const int d = 1 << j;
+    for (int t = threadIdx.x; t < nw; t += kSplitThreads)
+      nxt_t[t] = (Lvl)min((int)cur_t[t], t + d < nw ? (int)cur_t[t + d] : (int)Src::kNone);
+    __syncthreads();
+    Lvl* tmp = cur_t;
+    cur_t = nxt_t;
+    nxt_t = tmp;
   }
-  __syncthreads();
+  const int span = 1 << kd;
   uint32_t flags = 0;
   int cnt = 0;
 #pragma unroll
@@ -759,7 +1255,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_leaf_splits(const void* __res
       // windows j in [i - M, i - 1] (slots u .. u + M - 1, u = i - g0; slots of
       // invalid j hold kNone): split when the smallest window level is <= g
       const int u = (int)(i - g0);
-      const int wmin = min((int)s_suf[u], (int)s_pre[u + M - 1]);
+      const int wmin = min((int)cur_t[u], (int)cur_t[u + M - span]);
       f = f || wmin <= g;
     }
     flags |= (uint32_t)f << r;
@@ -1122,35 +1618,25 @@ __global__ void __launch_bounds__(256) k_coarse_splits(const int32_t* __restrict
 // Leaves: one warp per leaf reduces its points' bounding box.
 __global__ void k_leaf_nodes(const float4* __restrict__ pts, const int32_t* __restrict__ spl0,
                              NodeRec* __restrict__ nodes, const Meta* m) {
+  // one lane per leaf: a warp's 32 leaves are consecutive, so its lanes read
+  // neighbouring stretches of the sorted points and write consecutive records
   if (warp_failed(m)) return;
   const int64_t nn = m->n_nodes[0];
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int lane = lane_id();
-  for (int64_t L = gw; L < nn; L += nw) {
-    int64_t s = spl0[L], e = spl0[L + 1];
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < nn; L += nt) {
+    const int64_t s = spl0[L], e = spl0[L + 1];
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int64_t i = s + lane; i < e; i += 32) {
-      float4 p = pts[i];
+    for (int64_t i = s; i < e; ++i) {
+      const float4 p = pts[i];
       lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
       hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
     }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-        hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
-      }
-    }
-    if (lane == 0) {
-      NodeRec r;
-      r.lo[0] = lo[0]; r.lo[1] = lo[1]; r.lo[2] = lo[2];
-      r.hi[0] = hi[0]; r.hi[1] = hi[1]; r.hi[2] = hi[2];
-      r.count = (int32_t)(e - s);
-      r.first = (int32_t)s;
-      nodes[L] = r;
-    }
+    NodeRec r;
+    r.lo[0] = lo[0]; r.lo[1] = lo[1]; r.lo[2] = lo[2];
+    r.hi[0] = hi[0]; r.hi[1] = hi[1]; r.hi[2] = hi[2];
+    r.count = (int32_t)(e - s);
+    r.first = (int32_t)s;
+    nodes[L] = r;
   }
 }
 
@@ -1229,14 +1715,15 @@ void bbox_part(const float* d, int64_t n, float periodic_L, Meta* m, cudaStream_
   note_launch();
 }
 
-void keygen_part(const float* d, int64_t n, Meta* m, uint64_t* keys, cudaStream_t s) {
+void keygen_part(const float* d, int64_t n, Meta* m, uint64_t* keys, uint32_t* fine, int fshift,
+                 cudaStream_t s) {
   // the vectorised path loads float4 groups of points and stores key pairs as
   // 16-byte words: both addresses must be 16-byte aligned (the query part of a
   // two-set build starts at keys + n_src)
   const bool vec = (reinterpret_cast<uintptr_t>(d) & 15u) == 0 && (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
   const int gb = grid_for((n + 3) / 4, 256, 152 * 8);
-  if (vec) k_keygen<true><<<gb, 256, 0, s>>>(d, n, m, keys);
-  else k_keygen<false><<<gb, 256, 0, s>>>(d, n, m, keys);
+  if (vec) k_keygen<true><<<gb, 256, 0, s>>>(d, n, m, keys, fine, fshift);
+  else k_keygen<false><<<gb, 256, 0, s>>>(d, n, m, keys, fine, fshift);
   note_launch();
 }
 
@@ -1247,7 +1734,7 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
   Meta* m = at<Meta>(ws, L.meta);
   const int sms = 152;
   prof_begin(kPhBox, s);
-  k_init_meta<<<1, 256, 0, s>>>(m, L.n_planes); note_launch();
+  k_init_meta<<<1, 256, 0, s>>>(m, L.n_planes, L.bucket_sort); note_launch();
   bbox_part(d_a, n_a, periodic_L, m, s);
   if (n_b > 0) bbox_part(d_b, n_b, periodic_L, m, s);
   k_finish_box<<<1, 32, 0, s>>>(m, periodic_L); note_launch();
@@ -1280,16 +1767,50 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
   // the passes alternate between the two key buffers and must end in keys_a:
   // with an odd number of passes the keys start in keys_b
   uint64_t* keys_in = (kRadixPasses % 2) ? keys_b : keys_a;
-  keygen_part(d_a, n_a, m, keys_in, s);
-  if (n_b > 0) keygen_part(d_b, n_b, m, keys_in + n_a, s);
-  k_radix_offsets<<<1, 32 * kRadixPasses, 0, s>>>(m, kRadixPasses, kRadixBins); note_launch();
-  // look-back tables of all passes, zeroed once
   uint32_t* lookback = at<uint32_t>(ws, L.lookback);
+  // bucket sort: fine-bin counts, then first positions, and the scatter cursors
+  // live in the look-back area, which the LSD passes need only when they run
+  const int gated = L.bucket_sort ? 1 : 0;
+  const int64_t nbins = (int64_t)1 << L.fine_bits;
+  const int fshift = 3 * kKeyBits - L.fine_bits;
+  uint32_t* fine = L.bucket_sort ? lookback : nullptr;
+  uint32_t* fine_cur = lookback + nbins;
+  uint32_t* big = lookback + 2 * nbins;  // bins for k_big_bins (at most n / (kBinWarpMax + 1))
+  if (L.bucket_sort) {
+    k_zero_u64<<<grid_for(nbins / 2, 256, sms * 8), 256, 0, s>>>(reinterpret_cast<unsigned long long*>(fine),
+                                                                   nbins / 2);
+    note_launch();
+  }
+  keygen_part(d_a, n_a, m, keys_in, fine, fshift, s);
+  if (n_b > 0) keygen_part(d_b, n_b, m, keys_in + n_a, fine, fshift, s);
+  if (L.bucket_sort) {
+    unsigned long long* st = at<unsigned long long>(ws, L.scan_flags);
+    const int64_t ft = (nbins + kFineScanTile - 1) / kFineScanTile;
+    k_zero_u64<<<grid_for(ft, 256, sms * 8), 256, 0, s>>>(st, ft);
+    k_fine_scan<<<(unsigned)ft, 256, 0, s>>>(fine, fine_cur, nbins, st, m);
+    note_launch(2);
+    prof_end(kPhKeys, s);
+    prof_begin(kPhSort, s);
+    k_bucket_scatter<<<grid_for((n + 31) / 32 * 32 / kScatterRounds, 256, sms * 8), 256, 0, s>>>(
+        keys_in, n, fshift, fine_cur, keys_b, vals_b, m);
+    k_bin_sort<<<grid_for((nbins + 31) / 32 * 32, 256, sms * 8), 256, 0, s>>>(keys_b, vals_b, fine, nbins, n, keys_a,
+                                                                               d_a, d_b, n_a, pts, big, m);
+    const size_t gsm = sizeof(GrpSmem);
+    cudaFuncSetAttribute(k_big_bins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+    k_big_bins<<<sms * 2, kGrpThreads, gsm, s>>>(keys_b, vals_b, fine, big, nbins, n, keys_a, d_a, d_b, n_a, pts, m);
+    note_launch(3);
+    k_lsd_hist<<<grid_for((n + 3) / 4, 256, sms * 8), 256, 0, s>>>(keys_in, n, m);
+    note_launch();
+  }
+  k_radix_offsets<<<1, 32 * kRadixPasses, 0, s>>>(m, kRadixPasses, kRadixBins, gated); note_launch();
+  // look-back tables of all passes, zeroed once
   const int64_t lb_words = L.n_tiles_sort * kRadixBins * kRadixPasses;
-  k_zero_u64<<<grid_for(lb_words / 2 + 1, 256, sms * 8), 256, 0, s>>>(
-      reinterpret_cast<unsigned long long*>(lookback), (lb_words + 1) / 2); note_launch();
-  prof_end(kPhKeys, s);
-  prof_begin(kPhSort, s);
+  k_zero_u64_gated<<<grid_for(lb_words / 2 + 1, 256, sms * 8), 256, 0, s>>>(
+      reinterpret_cast<unsigned long long*>(lookback), (lb_words + 1) / 2, m); note_launch();
+  if (!L.bucket_sort) {
+    prof_end(kPhKeys, s);
+    prof_begin(kPhSort, s);
+  }
   const size_t smem = sizeof(SortSmem<kRadixBits>);
   cudaFuncSetAttribute(k_onesweep<kRadixBits, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k_onesweep<kRadixBits, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1301,10 +1822,10 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
     uint32_t* lb = lookback + (size_t)p * L.n_tiles_sort * kRadixBins;
     if (p + 1 < kRadixPasses) {
       k_onesweep<kRadixBits, false><<<(unsigned)L.n_tiles_sort, kSortThreads, smem, s>>>(
-          kin, vin, kout, vout, n, p, p * kRadixBits, lb, m, nullptr, nullptr, 0, nullptr);
+          kin, vin, kout, vout, n, p, p * kRadixBits, lb, m, nullptr, nullptr, 0, nullptr, gated);
     } else {  // last pass: the sorted points (gather) instead of the permutation
       k_onesweep<kRadixBits, true><<<(unsigned)L.n_tiles_sort, kSortThreads, smem, s>>>(
-          kin, vin, kout, nullptr, n, p, p * kRadixBits, lb, m, d_a, d_b, n_a, pts);
+          kin, vin, kout, nullptr, n, p, p * kRadixBits, lb, m, d_a, d_b, n_a, pts, gated);
     }
     note_launch();
     kin = kout;
@@ -1316,7 +1837,8 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
   prof_begin(kPhSplits, s);
   // plane 0: leaf splits, then n_i at every leaf split
   unsigned long long* st = at<unsigned long long>(ws, L.scan_flags);
-  const int64_t split_tiles = (n + 1 + kScanTile - 1) / kScanTile;
+  const int64_t leaf_tile = L.float_order ? FloatLevels::kTile : KeyLevels::kTile;
+  const int64_t split_tiles = (n + 1 + leaf_tile - 1) / leaf_tile;
   const bool reg = L.reg_fmax > 0.0f;
   // regularisation (Sec. II-D): after a plane's count splits, the volume classes
   // of its nodes give lvl_max^(p); the plane's splits are then taken again with
@@ -1360,7 +1882,7 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
   prof_end(kPhSplits, s);
   prof_begin(kPhNodes, s);
   // node records
-  k_leaf_nodes<<<grid_for((L.cap_nodes[0]) * 32, 256, sms * 16), 256, 0, s>>>(
+  k_leaf_nodes<<<grid_for(L.cap_nodes[0], 256, sms * 16), 256, 0, s>>>(
       pts, at<int32_t>(ws, L.spl[0]), at<NodeRec>(ws, L.nodes[0]), m); note_launch();
   for (int p = 1; p < L.n_planes; ++p) {
     k_upper_nodes<<<grid_for(L.cap_nodes[p] * 32, 256, sms * 16), 256, 0, s>>>(
@@ -1424,7 +1946,7 @@ void launch_sort_u64(uint64_t* k_a, uint64_t* k_b, uint32_t* v_a, uint32_t* v_b,
   const int64_t n_tiles = (n + kSortTile - 1) / kSortTile;
   k_sort_prep<<<1, 256, 0, s>>>(m); note_launch();
   k_key_hist<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(k_a, n, passes, m); note_launch();
-  k_radix_offsets<<<1, 32 * passes, 0, s>>>(m, passes, 256); note_launch();
+  k_radix_offsets<<<1, 32 * passes, 0, s>>>(m, passes, 256, 0); note_launch();
   const int64_t lb_words = n_tiles * 256 * passes;
   k_zero_u64<<<grid_for(lb_words / 2 + 1, 256, sms * 8), 256, 0, s>>>(
       reinterpret_cast<unsigned long long*>(lookback), (lb_words + 1) / 2); note_launch();
@@ -1436,7 +1958,7 @@ void launch_sort_u64(uint64_t* k_a, uint64_t* k_b, uint32_t* v_a, uint32_t* v_b,
   uint32_t* vout = v_b;
   for (int p = 0; p < passes; ++p) {
     k_onesweep<8, false><<<(unsigned)n_tiles, kSortThreads, smem, s>>>(
-        kin, vin, kout, vout, n, p, 8 * p, lookback + (size_t)p * n_tiles * 256, m, nullptr, nullptr, 0, nullptr);
+        kin, vin, kout, vout, n, p, 8 * p, lookback + (size_t)p * n_tiles * 256, m, nullptr, nullptr, 0, nullptr, 0);
     note_launch();
     kin = kout;
     vin = vout;

@@ -26,10 +26,23 @@ constexpr int kSortThreads = 256;
 constexpr int kSortIpt = 12;
 constexpr int kSortTile = kSortThreads * kSortIpt;  // 3072 keys per radix-sort tile
 constexpr int kScanTile = 1024;                      // elements per compaction tile
+// Bucket sort of the integer keys (sets of at least kBucketMinN points): one
+// scatter into 2^F fine bins (the top F key bits, F <= kMaxFineBits, about 32 to
+// 64 points per bin), then a sort of each bin (one warp in registers, or one
+// block of kGrpThreads in shared memory for bins of up to kGrpCap keys); taken
+// when no bin holds more than kGrpStep keys (else the LSD radix passes run).
+constexpr int64_t kBucketMinN = 1 << 16;
+constexpr int kMaxFineBits = 24;
+constexpr int kGrpThreads = 256;
+constexpr int kGrpIpt = 16;
+constexpr int kGrpCap = kGrpThreads * kGrpIpt;  // 4096 keys
+constexpr int kGrpStep = kGrpCap / 2;
+constexpr int kFineScanTile = 4096;             // fine bins per scan tile (256 threads x 16)
 constexpr int kMaxK = 32;        // neighbours per LeafToLeaf pass
 constexpr int kMaxKTotal = 256;  // neighbours per query (passes of kMaxK; one walk counter each)
 constexpr int kCtrLeafSplits = 8;
 constexpr int kCtrCoarse = 9;   // + plane
+constexpr int kCtrFine = 23;    // fine-bin scan of the bucket sort
 constexpr int kCtrWalk = 24;
 constexpr long long kSpinLimit = 1ll << 22;          // bounded waits (iterations)
 constexpr int kCasLimit = 1 << 20;                   // bounded union-find retries
@@ -66,7 +79,9 @@ struct Meta {
   unsigned long long arena_used;     // interaction-list entries handed out
   unsigned long long arena_peak;     // largest arena_used seen this walk
   int32_t n_planes;
-  int32_t pad;
+  uint32_t bucket_max;               // bucket sort: largest fine-bin count (above kGrpStep: LSD passes)
+  uint32_t big_bins;                 // bucket sort: bins left to k_big_bins
+  uint32_t big_next;                 // bucket sort: next listed bin to take
   unsigned long long knn_pairs;      // point pairs evaluated by the kNN LeafToLeaf
   unsigned long long knn_stats[8];   // kNN walk statistics (see jzt_status_info)
   unsigned long long knn_plane_entries[kMaxPlanes];  // interaction-list entries per plane
@@ -85,6 +100,8 @@ struct Layout {
   int32_t nmax0, c, n_target, ngr, heap;
   float reg_fmax;                     // 0: no regularisation
   int32_t float_order;                // 1: float z-order (no keys; pts_tmp is the sort's second buffer)
+  int32_t bucket_sort;                // 1: integer keys sorted by fine bins + group sorts (LSD passes as fallback)
+  int32_t fine_bits;                  // F: fine bins = the top F key bits
   int32_t n_planes;
   int64_t cap_nodes[kMaxPlanes + 1];  // [n_planes] = super-node capacity
   int64_t cap_ilist;                  // entries
@@ -149,6 +166,7 @@ struct Params {
   float fac_nodes, fac_ilist;
   float reg_fmax;
   int32_t float_order;  // 1: full-precision float z-order instead of integer keys
+  int32_t lsd_sort;     // 1: integer keys always by the LSD radix passes
 };
 
 // ---------------------------------------------------------------- host API

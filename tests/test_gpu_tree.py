@@ -97,3 +97,53 @@ def test_regularisation_leaves_results_unchanged():
         assert np.array_equal(da.cpu().numpy(), dr.cpu().numpy())
         b = 0.3 * workloads.mean_spacing(len(x))
         assert np.array_equal(a.fof(b).cpu().numpy(), r.fof(b).cpu().numpy())
+
+
+def _bucket_cases():
+    x_dup = workloads.uniform(1 << 17, 21)
+    x_dup[5000:5300] = x_dup[5000]       # 300 equal keys: the index passes restore input order
+    x_dup[90000:90007] = x_dup[12]       # equal keys written far apart in the input
+    x_heavy = workloads.uniform(1 << 17, 23)
+    x_heavy[:3000] = x_heavy[77]         # one fine bin above 2048 keys: the LSD passes run
+    return [
+        ("uniform-open-2^18", workloads.uniform(1 << 18, 20), 0.0, 1),
+        ("zeldovich-64^3", workloads.zeldovich(64, 3), 1.0, 1),
+        ("duplicates-2^17", x_dup, 0.0, 1),
+        ("ragged-65536+4093", workloads.uniform(65536 + 4093, 22), 1.0, 1),
+        ("heavy-bin-fallback", x_heavy, 1.0, 0),
+    ]
+
+
+@pytest.mark.parametrize("name,x,L,path", _bucket_cases(), ids=[c[0] for c in _bucket_cases()])
+def test_bucket_sort_matches_oracle(name, x, L, path):
+    """Sets of 2^16 points and more sort their keys by fine bins and per-group
+    shared-memory passes (LSD passes when a bin is too full): the same stable
+    order, gathered points and tree as the oracle, bit-exact, and the same
+    arrays as a build that forces the LSD passes."""
+    import paper_2604_05885_gb300 as jzt
+    xt = to_dev(x)
+    tree = jzt.build(xt, periodic_L=L)
+    st = tree.status()
+    assert st["code"] == 0, st
+    assert st["sort_path"] == path
+    keys, pts, n_planes = tree.arrays()
+    keys = keys.cpu().numpy().view(np.uint64)
+    p_np = pts.cpu().numpy()
+    sk, perm = oracle.zsort(oracle.morton_keys(x, L))
+    assert np.array_equal(keys, sk), f"sorted keys differ at {int(np.argmax(keys != sk))}"
+    assert np.array_equal(p_np[:, 3].view(np.int32), perm.astype(np.int32)), "sort order"
+    assert np.array_equal(p_np[:, :3], x[perm]), "gathered points"
+    spl_ref, gaps_ref = oracle.plane_splits(sk, nmax0=32, c=8, n_target=1000)  # library defaults
+    nodes_ref = oracle.plane_nodes(x[perm], gaps_ref)
+    assert n_planes == len(spl_ref)
+    lsd = jzt.build(xt, periodic_L=L, params=dict(lsd_sort=1))
+    assert lsd.status()["sort_path"] == 0
+    k2, p2, _ = lsd.arrays()
+    assert np.array_equal(k2.cpu().numpy().view(np.uint64), keys)
+    assert np.array_equal(p2.cpu().numpy().view(np.int32), p_np.view(np.int32))
+    for pl in range(n_planes):
+        spl, cnt, box = tree.plane(pl)
+        assert np.array_equal(spl, spl_ref[pl].astype(np.int32)), f"plane {pl} splits"
+        rc, rlo, rhi = nodes_ref[pl]
+        assert np.array_equal(cnt, rc.astype(np.int32)), f"plane {pl} counts"
+        assert np.array_equal(box[:, :3], rlo) and np.array_equal(box[:, 3:], rhi), f"plane {pl} boxes"
