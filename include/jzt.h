@@ -290,8 +290,8 @@ int jzt_batch_run_queue(const jzt_job *jobs, int n_jobs, const jzt_params *p, vo
  * a message naming the limit.  Calls no allocator.  The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
  * current, so make that first call before any stream capture; the address is kept
- * for the life of the process, so do not use this entry point after
- * cudaDeviceReset.  All calls share the one array per device: calls that overlap
+ * per device and CUDA context, and looked up again when the current context
+ * changes (after cudaDeviceReset, for instance).  All calls share the one array per device: calls that overlap
  * on the GPU (on different streams or threads) race and must be serialised by
  * the caller; each call re-initialises what it needs, the rest keeps the
  * previous call's data.

@@ -11,10 +11,12 @@
 // The array is g_noalloc_ws below (kNoAllocBytes, 16 MiB).  Every GPU that loads
 // the library holds it until the process exits.  In host code its name is only a
 // host-side stand-in for the device symbol, so its device address is looked up
-// with cudaGetSymbolAddress, once per device, with that device current, and that
-// address is what the kernels receive.  The cached address belongs to the CUDA
-// context of that first call: after cudaDeviceReset the entry point must not be
-// used again in the same process.
+// with cudaGetSymbolAddress, once per device and CUDA context, with that device
+// current, and that address is what the kernels receive.  The cache is keyed on
+// the current context as well, so that after cudaDeviceReset (a new primary
+// context, the module loaded again) the address is looked up afresh.  The first
+// call on a device (or in a new context) does this set-up and should come before
+// any stream capture.
 //
 // The interaction lists grow with the data (clustered or duplicate-heavy sets
 // need longer lists), so even within the size limits a call can run out of the
@@ -22,6 +24,7 @@
 // retry cures that; such a call fills every output row with index -1 and
 // distance NaN, so that a caller who does not read the status cannot mistake
 // the rows for results.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,21 +48,38 @@ __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocBytes];
 
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
+CUcontext g_ctx[kMaxDevices] = {};
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+CtxGetCurrent g_get_ctx = nullptr;
 
-// Device address of g_noalloc_ws on the current device (looked up on the
-// first call made on that device).
+// Device address of g_noalloc_ws on the current device, looked up on the first
+// call made on that device in its current context (cuCtxGetCurrent is reached
+// through the runtime's driver entry point, so the library needs no link to
+// the driver library).
 int scratch_address(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail_msg(JZT_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail_msg(JZT_ERR_UNSUPPORTED, "device ordinal out of range");
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  if (!g_get_ctx) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail_msg(JZT_ERR_CUDA, "cuCtxGetCurrent is not available from the driver");
+    g_get_ctx = reinterpret_cast<CtxGetCurrent>(fn);
+  }
+  CUcontext ctx = nullptr;  // null before the runtime has set up a context on this thread
+  if (g_get_ctx(&ctx) != CUDA_SUCCESS) return fail_msg(JZT_ERR_CUDA, "cuCtxGetCurrent failed");
+  if (!ctx || !g_addr[dev] || g_ctx[dev] != ctx) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+    e = cudaGetSymbolAddress(&p, g_noalloc_ws);  // sets up the context if there was none
     if (e != cudaSuccess || !p)
       return fail_msg(JZT_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    if (g_get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return fail_msg(JZT_ERR_CUDA, "no current CUDA context");
     g_addr[dev] = p;
+    g_ctx[dev] = ctx;
   }
   *out = g_addr[dev];
   return JZT_OK;
