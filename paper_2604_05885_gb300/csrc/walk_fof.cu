@@ -237,11 +237,13 @@ __global__ void __launch_bounds__(128) k_l2l_fof(const float4* __restrict__ pts,
                                                  const NodeRec* __restrict__ leaves,
                                                  const int2* __restrict__ arena, int32_t* ig_pt,
                                                  float L, float b2, Meta* m) {
+  __shared__ float4 s_b[128 / 32][32];  // per warp: the source leaf's points (leaves hold <= 32)
   if (failed(m)) return;
   const unsigned long long off = m->pair_off[0];
   const int64_t np = (int64_t)m->pair_cnt[0];
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int lane = lane_id();
+  float4* sb = s_b[warp_id()];
   const float invL = PER ? 1.0f / L : 0.0f;
   const float halfL = 0.5f * L;
   bool union_fail = false;
@@ -270,19 +272,26 @@ __global__ void __launch_bounds__(128) k_l2l_fof(const float4* __restrict__ pts,
         else ambiguous = true;
       }
     }
+    // the source points in shared memory (one coalesced load; leaves hold at most
+    // 32 points -- larger ranges are read from global memory)
+    const bool staged = B.count <= 32;
+    __syncwarp();
+    if (staged && lane < B.count) sb[lane] = pts[B.first + lane];
+    __syncwarp();
     for (int a0 = 0; a0 < A.count; a0 += 32) {
       const int ia = a0 + lane;
       const bool act = ia < A.count;
       const int a = A.first + ia;
       const float4 pa = act ? pts[a] : make_float4(0.f, 0.f, 0.f, 0.f);
-      // four source points per step: independent loads, the union only on a hit
+      // four source points per step, the union only on a hit
       constexpr int U = 4;
       for (int jb0 = self ? a0 : 0; jb0 < B.count; jb0 += U) {
         float d2[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int jb = jb0 + u;
-          const float4 pb = __ldg(pts + B.first + (jb < B.count ? jb : B.count - 1));
+          const int jc = jb < B.count ? jb : B.count - 1;
+          const float4 pb = staged ? sb[jc] : __ldg(pts + B.first + jc);
           float dx = pb.x - pa.x, dy = pb.y - pa.y, dz = pb.z - pa.z;
           if (PER) {
             if (ambiguous) {
