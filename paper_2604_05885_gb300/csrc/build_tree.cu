@@ -311,11 +311,14 @@ __device__ __forceinline__ void fine_count(uint32_t* __restrict__ fine, const ui
 }
 
 // Keys of all points plus either the digit histograms of the LSD passes
-// (fine == nullptr) or the counts of the 2^F fine bins (key >> fshift).
+// (fine == nullptr) or the counts of the 2^F fine bins (key >> fshift).  With
+// check_L > 0 (periodic boxes, whose quantisation box needs no pass over the
+// points) the coordinates are validated here instead of in k_bbox.
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_keygen(const float* __restrict__ xyz, int64_t n, Meta* m,
                                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ fine,
-                                                int fshift) {
+                                                int fshift, float check_L) {
+  bool bad = false;
   __shared__ uint32_t sh[kRadixPasses][kRadixBins];
   const bool digits = fine == nullptr;
   if (digits)
@@ -337,6 +340,11 @@ __global__ void __launch_bounds__(256) k_keygen(const float* __restrict__ xyz, i
       int cnt = 0;
       if (g < ng_full) {
         float4 a = __ldg(p4 + 3 * g), b = __ldg(p4 + 3 * g + 1), c = __ldg(p4 + 3 * g + 2);
+        if (check_L > 0.0f) {
+          const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+          for (int e = 0; e < 12; ++e) bad |= bad_coord(v[e], check_L);
+        }
         k4[0] = morton(a.x, a.y, a.z, lo, sc);
         k4[1] = morton(a.w, b.x, b.y, lo, sc);
         k4[2] = morton(b.z, b.w, c.x, lo, sc);
@@ -351,6 +359,9 @@ __global__ void __launch_bounds__(256) k_keygen(const float* __restrict__ xyz, i
         for (int e = 0; e < 4; ++e) {
           if (e < cnt) {
             const int64_t i = 4 * g + e;
+            if (check_L > 0.0f)
+              bad |= bad_coord(xyz[3 * i], check_L) || bad_coord(xyz[3 * i + 1], check_L) ||
+                     bad_coord(xyz[3 * i + 2], check_L);
             k4[e] = morton(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lo, sc);
             keys[i] = k4[e];
           }
@@ -369,6 +380,9 @@ __global__ void __launch_bounds__(256) k_keygen(const float* __restrict__ xyz, i
       int64_t i = r * nth + base_tid;
       uint64_t k = 0;
       if (i < n) {
+        if (check_L > 0.0f)
+          bad |= bad_coord(xyz[3 * i], check_L) || bad_coord(xyz[3 * i + 1], check_L) ||
+                 bad_coord(xyz[3 * i + 2], check_L);
         k = morton(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lo, sc);
         keys[i] = k;
       }
@@ -376,6 +390,7 @@ __global__ void __launch_bounds__(256) k_keygen(const float* __restrict__ xyz, i
       else if (i < n) atomicAdd(&fine[k >> fshift], 1u);
     }
   }
+  if (__any_sync(0xffffffffu, bad) && lane_id() == 0) set_error(m, JZT_ERR_INPUT, kStageInput);
   if (!digits) return;
   __syncthreads();
   for (int i = threadIdx.x; i < kRadixPasses * kRadixBins; i += blockDim.x) {
@@ -1716,14 +1731,14 @@ void bbox_part(const float* d, int64_t n, float periodic_L, Meta* m, cudaStream_
 }
 
 void keygen_part(const float* d, int64_t n, Meta* m, uint64_t* keys, uint32_t* fine, int fshift,
-                 cudaStream_t s) {
+                 float check_L, cudaStream_t s) {
   // the vectorised path loads float4 groups of points and stores key pairs as
   // 16-byte words: both addresses must be 16-byte aligned (the query part of a
   // two-set build starts at keys + n_src)
   const bool vec = (reinterpret_cast<uintptr_t>(d) & 15u) == 0 && (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
   const int gb = grid_for((n + 3) / 4, 256, 152 * 8);
-  if (vec) k_keygen<true><<<gb, 256, 0, s>>>(d, n, m, keys, fine, fshift);
-  else k_keygen<false><<<gb, 256, 0, s>>>(d, n, m, keys, fine, fshift);
+  if (vec) k_keygen<true><<<gb, 256, 0, s>>>(d, n, m, keys, fine, fshift, check_L);
+  else k_keygen<false><<<gb, 256, 0, s>>>(d, n, m, keys, fine, fshift, check_L);
   note_launch();
 }
 
@@ -1735,8 +1750,12 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
   const int sms = 152;
   prof_begin(kPhBox, s);
   k_init_meta<<<1, 256, 0, s>>>(m, L.n_planes, L.bucket_sort); note_launch();
-  bbox_part(d_a, n_a, periodic_L, m, s);
-  if (n_b > 0) bbox_part(d_b, n_b, periodic_L, m, s);
+  // periodic boxes with integer keys: the key generation validates the points
+  const bool check_in_keys = !L.float_order && periodic_L > 0.0f;
+  if (!check_in_keys) {
+    bbox_part(d_a, n_a, periodic_L, m, s);
+    if (n_b > 0) bbox_part(d_b, n_b, periodic_L, m, s);
+  }
   k_finish_box<<<1, 32, 0, s>>>(m, periodic_L); note_launch();
   prof_end(kPhBox, s);
   uint64_t* keys_a = at<uint64_t>(ws, L.keys_a);
@@ -1781,8 +1800,9 @@ void build_impl(const float* d_a, int64_t n_a, const float* d_b, int64_t n_b, fl
                                                                    nbins / 2);
     note_launch();
   }
-  keygen_part(d_a, n_a, m, keys_in, fine, fshift, s);
-  if (n_b > 0) keygen_part(d_b, n_b, m, keys_in + n_a, fine, fshift, s);
+  const float check_L = check_in_keys ? periodic_L : 0.0f;
+  keygen_part(d_a, n_a, m, keys_in, fine, fshift, check_L, s);
+  if (n_b > 0) keygen_part(d_b, n_b, m, keys_in + n_a, fine, fshift, check_L, s);
   if (L.bucket_sort) {
     unsigned long long* st = at<unsigned long long>(ws, L.scan_flags);
     const int64_t ft = (nbins + kFineScanTile - 1) / kFineScanTile;
