@@ -546,7 +546,60 @@ __device__ __forceinline__ void sort_list(IEntry* list, uint32_t cnt) {
   }
 }
 
+// Lists of 129..256 entries: the same order by a bitonic network in shared
+// memory (the warp's 256 slots), so that the register-resident sorts above stay
+// small and the kernel keeps many warps per SM.
+__device__ __noinline__ void sort_list_smem(IEntry* list, uint32_t cnt, unsigned long long* buf) {
+  const int lane = lane_id();
+  for (uint32_t i = lane; i < 256; i += 32) {
+    if (i < cnt) {
+      const IEntry x = list[i];
+      buf[i] = ((unsigned long long)__float_as_uint(x.r2low) << 32) | (uint32_t)x.src;
+    } else {
+      buf[i] = ~0ull;
+    }
+  }
+  __syncwarp();
+  for (int size = 2; size <= 256; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int q = lane; q < 128; q += 32) {  // pair q: lower index i, partner i + stride
+        const int i = ((q / stride) * 2 * stride) + (q % stride);
+        const int j = i + stride;
+        const bool up = (i & size) == 0;
+        const unsigned long long a = buf[i], b = buf[j];
+        if ((a > b) == up) {
+          buf[i] = b;
+          buf[j] = a;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // r_low^2 halves made suffix minima (bf16, rounded down), written back unpacked
+  uint32_t later = 0x7f80u;
+  for (int c = 7; c >= 0; --c) {  // chunks of 32 from the end
+    const uint32_t i = 32u * c + lane;
+    uint32_t r = i < cnt ? (uint32_t)((buf[i] >> 32) & 0xffffu) : 0x7f80u;
+    // suffix minimum within the chunk (lanes >= lane), then with the later chunks
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_down_sync(kFull, r, o);
+      if (lane + o < 32) r = min(r, t);
+    }
+    r = min(r, later);
+    later = __shfl_sync(kFull, r, 0);
+    if (i < cnt) {
+      IEntry x;
+      x.src = (int32_t)(uint32_t)(buf[i] & 0xffffffffull);
+      x.r2low = __uint_as_float(r << 16);
+      list[i] = x;
+    }
+  }
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(128) k_sort_lists(uint2* ilo, IEntry* arena, int plane, Meta* m) {
+  __shared__ unsigned long long s_buf[4][256];
   if (warp_failed(m)) return;
   const int64_t nn = m->n_nodes[plane];
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -557,7 +610,7 @@ __global__ void __launch_bounds__(128) k_sort_lists(uint2* ilo, IEntry* arena, i
     if (cnt <= 32) sort_list<1>(list, cnt);
     else if (cnt <= 64) sort_list<2>(list, cnt);
     else if (cnt <= 128) sort_list<4>(list, cnt);
-    else if (cnt <= 256) sort_list<8>(list, cnt);
+    else if (cnt <= 256) sort_list_smem(list, cnt, s_buf[warp_id()]);
     else {
       for (uint32_t i = lane_id(); i < cnt; i += 32) {
         IEntry x = list[i];
