@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--n-side", type=int, default=512)
     ap.add_argument("--k", type=int, default=16)
     ap.add_argument("--b-frac", type=float, default=0.2)
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--ref-queries", type=int, default=1 << 18,
                     help="kNN rows per step of --impl reference (random points of the full set)")
     ap.add_argument("--ref-side", type=float, default=0.25,
