@@ -77,3 +77,15 @@ def test_query_tree_rejects_fof_and_large_k():
         tree.knn(101)
     assert e.value.code == jzt.JZT_ERR_INVALID
     torch.cuda.synchronize()
+
+
+def test_query_sets_on_the_bucket_sort():
+    """A combined set of 2^16 points and more sorts its keys by fine bins (sources
+    and queries under one index): rows as the all-pairs oracle's."""
+    import paper_2604_05885_gb300 as jzt
+    src, qry = workloads.uniform(60000, 931), workloads.uniform(10000, 932)
+    tree = jzt.build_query(to_dev(src), to_dev(qry), periodic_L=1.0, k_max=16)
+    idx, d2 = tree.knn(16)
+    st = tree.status()
+    assert st["code"] == 0 and st["sort_path"] == 1
+    _check(src, qry, 16, 1.0, idx, d2)

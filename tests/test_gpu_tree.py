@@ -105,11 +105,15 @@ def _bucket_cases():
     x_dup[90000:90007] = x_dup[12]       # equal keys written far apart in the input
     x_heavy = workloads.uniform(1 << 17, 23)
     x_heavy[:3000] = x_heavy[77]         # one fine bin above 2048 keys: the LSD passes run
+    rng = np.random.default_rng(24)      # a dense blob: one bin of ~1500 distinct keys (block sort)
+    x_blob = workloads.uniform(1 << 17, 24)
+    x_blob[:1500] = workloads.clip_unit(rng.normal(0.3, 5e-5, (1500, 3)))  # no two keys equal
     return [
         ("uniform-open-2^18", workloads.uniform(1 << 18, 20), 0.0, 1),
         ("zeldovich-64^3", workloads.zeldovich(64, 3), 1.0, 1),
         ("duplicates-2^17", x_dup, 0.0, 1),
         ("ragged-65536+4093", workloads.uniform(65536 + 4093, 22), 1.0, 1),
+        ("dense-blob-big-bin", x_blob, 0.0, 1),
         ("heavy-bin-fallback", x_heavy, 1.0, 0),
     ]
 
