@@ -47,8 +47,10 @@ def test_workspace_bytes_grows_and_validates():
     assert jzt.workspace_bytes(1000, 256) > jzt.workspace_bytes(1000, 32)
     with pytest.raises(jzt.JztError):
         jzt.workspace_bytes(100, 257)
+    # the key sort's choice changes no workspace part
+    assert jzt.workspace_bytes(1 << 20, 16, {"lsd_sort": 1}) == jzt.workspace_bytes(1 << 20, 16)
     for p in ({"nmax0": 33}, {"nmax0": -1}, {"plane_factor": 1}, {"heap_size": 17},
-              {"alloc_fac_ilist": -1.0}):
+              {"alloc_fac_ilist": -1.0}, {"lsd_sort": 2}, {"lsd_sort": -1}):
         with pytest.raises(jzt.JztError) as e:
             jzt.workspace_bytes(1000, 0, p)
         assert e.value.code == jzt.JZT_ERR_INVALID
