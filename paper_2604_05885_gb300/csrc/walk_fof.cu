@@ -278,13 +278,49 @@ __global__ void __launch_bounds__(128) k_l2l_fof(const float4* __restrict__ pts,
     __syncwarp();
     if (staged && lane < B.count) sb[lane] = pts[B.first + lane];
     __syncwarp();
+    constexpr int U = 4;  // source points per step, the union only on a hit
+    if (self && staged) {
+      // a leaf with itself: lane a takes the partners (a + d) mod c, d = 1 .. c/2
+      // (d = c/2 of an even c from the lower half only), so every unordered pair
+      // is tested exactly once and the lanes share the triangle evenly.  d^2
+      // does not depend on the pair's orientation: the differences only change
+      // sign (the image shift of a leaf with itself is zero or the minimum image).
+      const int c = A.count, half = c / 2;
+      const bool act = lane < c;
+      const float4 pa = act ? sb[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int d0 = 1; d0 <= half; d0 += U) {
+        float d2[U];
+        int pb_i[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int d = d0 + u;
+          int bi = lane + d;
+          if (bi >= c) bi -= c;
+          const bool ok = act && d <= half && !(2 * d == c && lane >= half);
+          pb_i[u] = ok ? bi : 0;
+          const float4 pb = sb[pb_i[u]];
+          float dx = pb.x - pa.x, dy = pb.y - pa.y, dz = pb.z - pa.z;
+          if (PER && ambiguous) {
+            dx = wrap1(dx, L, invL);
+            dy = wrap1(dy, L, invL);
+            dz = wrap1(dz, L, invL);
+          }
+          d2[u] = ok ? __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) : INFINITY;
+        }
+        const bool any = d2[0] <= b2 || d2[1] <= b2 || d2[2] <= b2 || d2[3] <= b2;
+        if (any) {
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (d2[u] <= b2 && !uf_union(ig_pt, A.first + lane, A.first + pb_i[u])) union_fail = true;
+        }
+      }
+      continue;
+    }
     for (int a0 = 0; a0 < A.count; a0 += 32) {
       const int ia = a0 + lane;
       const bool act = ia < A.count;
       const int a = A.first + ia;
       const float4 pa = act ? pts[a] : make_float4(0.f, 0.f, 0.f, 0.f);
-      // four source points per step, the union only on a hit
-      constexpr int U = 4;
       for (int jb0 = self ? a0 : 0; jb0 < B.count; jb0 += U) {
         float d2[U];
 #pragma unroll
