@@ -357,18 +357,29 @@ __global__ void __launch_bounds__(128) k_l2l_fof(const float4* __restrict__ pts,
   if (lane == 0 && pairs) atomicAdd(&m->fof_pairs, pairs);
 }
 
-__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
+// Smallest original index per root, then labels in input order.
+// Point roots after the final contraction; a root starts its group's minimum
+// with its own original index (only roots' entries of minorig are ever read).
+__global__ void k_contract_points(int32_t* ig_pt, const float4* __restrict__ pts, int32_t* minorig, int64_t n,
+                                  const Meta* m) {
+  if (failed(m)) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = v;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = uf_root_ro(ig_pt, (int)i);
+    ig_pt[i] = r;
+    if (r == (int)i) minorig[i] = __float_as_int(pts[i].w);
+  }
 }
 
-// Smallest original index per root, then labels in input order.
+// The other members lower their root's minimum (singletons, most points at small
+// linking lengths, need no atomic).
 __global__ void k_group_min(const float4* __restrict__ pts, const int32_t* __restrict__ ig_pt,
                             int32_t* minorig, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    atomicMin(&minorig[ig_pt[i]], __float_as_int(pts[i].w));
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = ig_pt[i];
+    if (r != (int)i) atomicMin(&minorig[r], __float_as_int(pts[i].w));
+  }
 }
 
 __global__ void k_labels(const float4* __restrict__ pts, const int32_t* __restrict__ ig_pt,
@@ -429,9 +440,9 @@ void fof_all(const Layout& L, char* ws, float pl, float b, int32_t* labels, cuda
                                           ig_pt, pl, b2, m); note_launch();
   prof_end(kPhFofL2L, s);
   prof_begin(kPhFofLabels, s);
-  k_contract<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(ig_pt, -1, n, m); note_launch();
   int32_t* minorig = at<int32_t>(ws, L.minorig);
-  k_fill_i32<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(minorig, n, INT_MAX); note_launch();
+  k_contract_points<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(ig_pt, at<float4>(ws, L.pts), minorig, n, m);
+  note_launch();
   k_group_min<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(at<float4>(ws, L.pts), ig_pt, minorig, n); note_launch();
   k_labels<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(at<float4>(ws, L.pts), ig_pt, minorig, labels, n, m); note_launch();
   prof_end(kPhFofLabels, s);
