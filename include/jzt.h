@@ -68,12 +68,13 @@ typedef struct jzt_params {
                                  comparator; Eq. lvl at float32 precision), for data whose scales
                                  span many orders of magnitude -- results do not change, only the
                                  tree; needs 16 more workspace bytes per point; not with reg_fmax */
-    int32_t lsd_sort;         /* sort of the integer keys (Sec. II-B; the result is the same stable
-                                 order either way): 0 (default) = for N >= 2^16 one scatter of the
-                                 keys into fine bins (their top bits) and one shared-memory sort
-                                 per group of consecutive bins, taken when no fine bin holds more
-                                 than 2048 points and replaced on the device by the LSD radix
-                                 passes otherwise; 1 = always the LSD radix passes */
+    int32_t lsd_sort;         /* sort of the integer keys (Sec. II-A, z-order sort; the result is the
+                                 same stable order either way): 0 (default) = for N >= 2^16 one
+                                 scatter of the keys into fine bins (their top bits) and one sort
+                                 per bin (a warp's registers; a block's shared memory above 128
+                                 keys), taken when no fine bin holds more than 2048 points and
+                                 replaced on the device by the LSD radix passes otherwise;
+                                 1 = always the LSD radix passes */
     int32_t reserved[4];      /* must be zero */
 } jzt_params;
 
