@@ -279,8 +279,13 @@ __global__ void __launch_bounds__(32 * kN2NWarps) k_n2n_knn(const int32_t* __res
   const int lane = lane_id();
   N2NWarpSmem& S = S_all[warp_id()];
   const int64_t npar = m->n_nodes[par_plane];
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t P = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; P < npar; P += nw) {
+  // parents are taken one at a time from a shared counter (their cost varies with
+  // their children and lists; a fixed stride left warps idle at the end)
+  while (true) {
+    int64_t P = 0;
+    if (lane == 0) P = atomicAdd(&m->tile_ctr[kCtrN2N], 1u);
+    P = __shfl_sync(kFull, P, 0);
+    if (P >= npar) break;
     const int c_begin = spl_par[P], c_end = spl_par[P + 1];
     const uint2 lo = ilo_par[P];
     const uint32_t e_off = lo.x, e_cnt = lo.y & ~kUnsortedBit;
@@ -1231,6 +1236,7 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX))
 // Interaction-list entries written by one plane's NodeToNode (arena growth).
 __global__ void k_plane_mark(Meta* m, int plane, int end) {
   if (threadIdx.x != 0) return;
+  if (!end) m->tile_ctr[kCtrN2N] = 0;  // the plane's NodeToNode takes parents from here
   if (!end) m->knn_plane_entries[plane] = m->arena_used;
   else m->knn_plane_entries[plane] = m->arena_used - m->knn_plane_entries[plane];
 }
