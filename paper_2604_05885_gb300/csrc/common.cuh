@@ -44,6 +44,7 @@ constexpr int kCtrLeafSplits = 8;
 constexpr int kCtrCoarse = 9;   // + plane
 constexpr int kCtrFine = 23;    // fine-bin scan of the bucket sort
 constexpr int kCtrN2N = 7;      // kNN NodeToNode parents (walk only: the build's radix passes are done)
+constexpr int kCtrLists = 6;    // kNN list sort (walk only, as above)
 constexpr int kCtrWalk = 24;
 constexpr long long kSpinLimit = 1ll << 22;          // bounded waits (iterations)
 constexpr int kCasLimit = 1 << 20;                   // bounded union-find retries

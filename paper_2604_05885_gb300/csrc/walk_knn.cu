@@ -607,8 +607,12 @@ __global__ void __launch_bounds__(128) k_sort_lists(uint2* ilo, IEntry* arena, i
   __shared__ unsigned long long s_buf[4][256];
   if (warp_failed(m)) return;
   const int64_t nn = m->n_nodes[plane];
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < nn; c += nw) {
+  // lists are taken one at a time from a device counter (their lengths vary)
+  while (true) {
+    int64_t c = 0;
+    if (lane_id() == 0) c = atomicAdd(&m->tile_ctr[kCtrLists], 1u);
+    c = __shfl_sync(kFull, c, 0);
+    if (c >= nn) break;
     const uint2 lo = ilo[c];
     const uint32_t cnt = lo.y;
     IEntry* list = arena + lo.x;
@@ -1237,6 +1241,7 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX))
 __global__ void k_plane_mark(Meta* m, int plane, int end) {
   if (threadIdx.x != 0) return;
   if (!end) m->tile_ctr[kCtrN2N] = 0;  // the plane's NodeToNode takes parents from here
+  else m->tile_ctr[kCtrLists] = 0;    // and the list sort after it, lists
   if (!end) m->knn_plane_entries[plane] = m->arena_used;
   else m->knn_plane_entries[plane] = m->arena_used - m->knn_plane_entries[plane];
 }
