@@ -357,9 +357,9 @@ __global__ void __launch_bounds__(128) k_l2l_fof(const float4* __restrict__ pts,
   if (lane == 0 && pairs) atomicAdd(&m->fof_pairs, pairs);
 }
 
-// Smallest original index per root, then labels in input order.
-// Point roots after the final contraction; a root starts its group's minimum
-// with its own original index (only roots' entries of minorig are ever read).
+// Canonical labels: point roots after the final contraction (a root starts its
+// group's minimum original index with its own; only roots' entries of minorig
+// are ever read), the members' minimum, then the labels in input order.
 __global__ void k_contract_points(int32_t* ig_pt, const float4* __restrict__ pts, int32_t* minorig, int64_t n,
                                   const Meta* m) {
   if (failed(m)) return;

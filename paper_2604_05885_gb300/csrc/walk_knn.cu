@@ -1240,8 +1240,8 @@ __global__ void __launch_bounds__(32 * kL2LWarps, JZT_L2L_MINBLOCKS(KMAX))
 // Interaction-list entries written by one plane's NodeToNode (arena growth).
 __global__ void k_plane_mark(Meta* m, int plane, int end) {
   if (threadIdx.x != 0) return;
-  if (!end) m->tile_ctr[kCtrN2N] = 0;  // the plane's NodeToNode takes parents from here
-  else m->tile_ctr[kCtrLists] = 0;    // and the list sort after it, lists
+  if (!end) m->tile_ctr[kCtrN2N] = 0;  // the plane's NodeToNode takes its parents from here
+  else m->tile_ctr[kCtrLists] = 0;    // the list sort that follows takes its lists from here
   if (!end) m->knn_plane_entries[plane] = m->arena_used;
   else m->knn_plane_entries[plane] = m->arena_used - m->knn_plane_entries[plane];
 }
