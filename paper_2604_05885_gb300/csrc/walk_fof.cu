@@ -19,7 +19,6 @@
 // range with one atomic.
 #include <cuda_runtime.h>
 
-#include <climits>
 
 #include "common.cuh"
 
